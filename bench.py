@@ -1,0 +1,370 @@
+"""Benchmark of the DFT+U (ACBN0) Hubbard-projector pass on GB300.
+
+One step = one pass of the whole hot path over the oxide supercell (periodic 96^3 grid at 0.25 bohr,
+8 transition-metal d shells + 8 oxygen p shells, 256 bands, 8 k-points, collinear spin):
+    project -> occupations (n, Nbar, Pbar) -> ACBN0 U, J, E_U, V -> apply (psi += V_U psi, in place)
+through the C ABI.  The metric is algorithmic GB/s of that pass: every sphere point of every state is
+read by the projection and read + written by the apply (complex128: 16 B per point).
+
+Prints ONE JSON line (rank 0).  --impl reference times the CPU FP64 oracle on a bounded sample of the
+same workload instead.  Under torchrun every rank runs an independent replica (the pass has no
+cross-GPU exchange in this build), timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DFT+U projector GB/s & %HBM peak; FP32-state vs FP64 speedup at |dn|<=1e-6"
+UNIT = "GB/s"
+WORKLOAD = "oxide supercell 96^3 h=0.25, 8 TM(3d,R4.5)+8 O(2p,R3.5), 256 bands, 8 k, collinear, FP64 states"
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return float(d.get("hbm_gbs")), "measured (MEASURED_PEAKS.json)"
+        except Exception:
+            pass
+    return 6800.0, "fallback (6.8 TB/s, profiling recipe)"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            for n, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def algorithmic_bytes(handle_npts, nbands, nk, ns, bytes_per_point, orbitals_bytes):
+    """(projection bytes, apply bytes) of one pass: every sphere point of every state once for the
+    projection (plus the orbital table once), twice (read + write) for the apply."""
+    pts = int(sum(handle_npts))
+    states = pts * bytes_per_point * nbands * nk * ns
+    return states + orbitals_bytes, 2 * states + orbitals_bytes
+
+
+def run_ours(args):
+    import torch
+    from paper_1711_08935_gb300 import dftu, synth
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    s = synth.oxide_system(n=args.grid, nk=args.nkgrid)
+    nb = args.nbands
+    nocc = nb // 2
+    t0 = time.time()
+    psi = synth.make_states(s, nb, seed=2, device=dev, spin_bias=synth.afm_spin_bias(s))
+    gen_s = time.time() - t0
+    f = torch.from_numpy(synth.step_occupations(s.nk, 2, nb, nocc)).to(dev)
+    h = dftu.handle_for_system(s, nb, device=local)
+    for sp in range(len(s.radials)):
+        h.coulomb_integrals(sp)
+    npts = [h.lib.dftu_atom_points(h.h, i) for i in range(len(s.atoms))]
+    MT = h.lib.dftu_total_orbitals(h.h)
+    orb_bytes = sum(n * (2 * a.l + 1) * 8 for n, a in zip(npts, s.atoms))
+    stream = torch.cuda.current_stream(dev)
+
+    # ---- precision check on identical inputs before any apply: FP32-state vs FP64 occupations
+    psi32 = psi.to(torch.complex64)
+    h.project(psi); h.occupations(f); h.acbn0_uj()
+    r64 = h.results()
+    h.project(psi32); h.occupations(f); h.acbn0_uj()
+    r32 = h.results()
+    max_dn = max(float(np.max(np.abs(a - b))) for a, b in zip(r64["n"], r32["n"]))
+    dU = float(np.max(np.abs(r64["U"] - r32["U"]))) * dftu.HARTREE_EV
+    dJ = float(np.max(np.abs(r64["J"] - r32["J"]))) * dftu.HARTREE_EV
+    dE = abs(r64["EU"] - r32["EU"]) * dftu.HARTREE_EV
+
+    def step(x):
+        h.project(x)
+        h.occupations(f)
+        h.acbn0_uj()
+        h.apply(x)
+
+    def timed(x, steps, warmup):
+        for _ in range(warmup):
+            step(x)
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+               torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+               torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for i in range(steps):
+            e0, e1, e2, e3, e4 = ev[i]
+            e0.record(stream)
+            h.project(x)
+            e1.record(stream)
+            h.occupations(f)
+            h.acbn0_uj()
+            e2.record(stream)
+            e3.record(stream)
+            h.apply(x)
+            e4.record(stream)
+        end.record(stream)
+        torch.cuda.synchronize()
+        total = start.elapsed_time(end)
+        proj = [e[0].elapsed_time(e[1]) for e in ev]
+        small = [e[1].elapsed_time(e[2]) for e in ev]
+        app = [e[3].elapsed_time(e[4]) for e in ev]
+        return total / steps, statistics.mean(proj), statistics.mean(small), statistics.mean(app)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms64, proj64, small64, app64 = timed(psi, args.steps, args.warmup)
+    clk = clocks.stop()
+    del psi
+    torch.cuda.empty_cache()
+    ms32, proj32, small32, app32 = timed(psi32, args.steps, args.warmup)
+    status = h.sync_status()
+
+    pb64, ab64 = algorithmic_bytes(npts, nb, s.nk, 2, 16, orb_bytes)
+    pb32, ab32 = algorithmic_bytes(npts, nb, s.nk, 2, 8, orb_bytes)
+    step_bytes64 = pb64 + ab64
+    if ws > 1:
+        t = torch.tensor([ms64, ms32], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms64, ms32 = float(t[0]), float(t[1])
+    value = ws * step_bytes64 / (ms64 * 1e-3) / 1e9
+    peak, peak_src = measured_peaks()
+    # dominant kernel by time: the apply (read + write of every sphere point)
+    dom = "apply" if app64 >= proj64 else "project"
+    dom_ms = app64 if dom == "apply" else proj64
+    dom_bytes = ab64 if dom == "apply" else pb64
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+
+    # ---- end to end through the public API with host (pinned) states
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, h, s, nb, f, dev, step_bytes64, ws)
+
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms64, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c128 states; FP32-pair arithmetic (~2^-44) for products, FP64 occupations/U/J",
+        "data": "synthetic (seeded Gaussian-type Bloch states, orthonormalised; hydrogenic radial orbitals)",
+        "config": {"workload": WORKLOAD, "global_batch": nb * s.nk * 2 * ws, "seq_len": int(sum(npts)),
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "l2": "inputs (58 GB of states) far larger than L2; no flush needed",
+                   "sphere_points": int(sum(npts)), "bands": nb, "kpoints": s.nk, "spins": 2},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_source": peak_src, "traffic": None,
+                     "bytes_per_launch": dom_bytes},
+        "kernels_ms": {"project": round(proj64, 4), "occupations+acbn0": round(small64, 4), "apply": round(app64, 4),
+                       "project_GBps": round(pb64 / (proj64 * 1e-3) / 1e9, 1),
+                       "apply_GBps": round(ab64 / (app64 * 1e-3) / 1e9, 1)},
+        "fp32_state": {"ms_per_step": round(ms32, 4), "GBps": round((pb32 + ab32) / (ms32 * 1e-3) / 1e9, 2),
+                       "speedup_vs_fp64": round(ms64 / ms32, 3), "max_abs_dn": max_dn, "max_dU_eV": dU, "max_dJ_eV": dJ,
+                       "dEU_eV": dE, "project_ms": round(proj32, 4), "apply_ms": round(app32, 4)},
+        "results": {"U_eV": [round(x * dftu.HARTREE_EV, 6) for x in r64["U"]],
+                    "J_eV": [round(x * dftu.HARTREE_EV, 6) for x in r64["J"]], "EU_eV": r64["EU"] * dftu.HARTREE_EV},
+        "clocks": clk, "e2e": e2e, "gpu_launches": None, "device_status": int(status),
+        "state_generation_s": round(gen_s, 1),
+    }
+    # our kernel launches in the timed FP64 region: project (2), occupations (2), acbn0 (1), apply (1 per colour;
+    # the oxide spheres do not overlap, so one colour)
+    line["gpu_launches"] = (2 + 2 + 1 + 1) * args.steps
+    if not args.no_cpu_baseline and rank == 0:
+        line["cpu_baseline"] = cpu_baseline(args, s)
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_e2e(args, h, s, nb, f, dev, step_bytes, ws):
+    """Per step: pinned host states -> device, the pass, results (n, U, J, E_U) -> host."""
+    import torch
+    from paper_1711_08935_gb300 import synth
+    host = torch.empty((s.nk, 2, nb, s.grid.npts), dtype=torch.complex128, pin_memory=True)
+    gen = synth.make_states(s, nb, seed=7, device=dev, spin_bias=synth.afm_spin_bias(s))
+    host.copy_(gen)
+    del gen
+    dbuf = torch.empty_like(host, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    n_steps = max(1, min(args.steps, 3))
+
+    def one():
+        dbuf.copy_(host, non_blocking=True)
+        h.project(dbuf)
+        h.occupations(f)
+        h.acbn0_uj()
+        h.apply(dbuf)
+        return h.results()
+
+    one()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_steps):
+        r = one()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / n_steps
+    h2d = host.numel() * 16
+    d2h = sum(x.size for x in r["n"]) * 16 + 3 * len(s.atoms) * 8 + 8
+    del dbuf, host
+    torch.cuda.empty_cache()
+    return {"value": round(ws * step_bytes / dt / 1e9, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "steps": n_steps, "ms_per_step": round(dt * 1e3, 2)}
+
+
+def cpu_baseline(args, s, target_s=15.0):
+    """The CPU FP64 oracle, as it stands, on a bounded sample of the same workload: one k-point, one
+    spin channel, a few bands (project + occupations + U/J + apply for those states)."""
+    import torch
+    from oracle import dftu_oracle as O
+    from paper_1711_08935_gb300 import synth
+    st = O.setup_atoms(s)
+    coul = []
+    for sp in range(len(s.radials)):
+        I = [a.species for a in s.atoms].index(sp)
+        coul.append(O.coulomb_integrals(s.grid, s.atoms[I], st[I]))
+    nbs = 4
+    sub = synth.System(s.grid, s.atoms, s.radials, s.kpts[:1], np.ones(1), nspin=2)
+    psi = synth.make_states(sub, nbs, seed=11, device="cpu").numpy()
+    f = np.ones((1, 2, nbs))
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        O.hubbard_pass(sub, st, psi, f, coulomb=coul)
+        reps += 1
+        if time.perf_counter() - t0 > target_s:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    pts = sum(len(x["idx"]) for x in st)
+    bytes_ = 3 * pts * 16 * nbs * 2
+    try:
+        import threadpoolctl
+        cores = max(i.get("num_threads", 1) for i in threadpoolctl.threadpool_info()) or 1
+    except Exception:
+        cores = os.cpu_count()
+    return {"value": round(bytes_ / dt / 1e9, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"1 k-point x 2 spins x {nbs} bands of the same 96^3 oxide workload, full pass, {reps} reps, {dt:.2f} s/pass"}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from paper_1711_08935_gb300 import synth
+    s = synth.oxide_system(n=args.grid, nk=args.nkgrid)
+    from oracle import dftu_oracle as O
+    st = O.setup_atoms(s)
+    coul = []
+    for sp in range(len(s.radials)):
+        I = [a.species for a in s.atoms].index(sp)
+        coul.append(O.coulomb_integrals(s.grid, s.atoms[I], st[I]))
+    nbs = 2
+    sub = synth.System(s.grid, s.atoms, s.radials, s.kpts[:1], np.ones(1), nspin=2)
+    psi = synth.make_states(sub, nbs, seed=11, device="cpu").numpy()
+    f = np.ones((1, 2, nbs))
+    for _ in range(args.warmup):
+        O.hubbard_pass(sub, st, psi, f, coulomb=coul)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.hubbard_pass(sub, st, psi, f, coulomb=coul)
+    dt = (time.perf_counter() - t0) / args.steps
+    pts = sum(len(x["idx"]) for x in st)
+    value = 3 * pts * 16 * nbs * 2 / dt / 1e9
+    try:
+        import threadpoolctl
+        cores = max(i.get("num_threads", 1) for i in threadpoolctl.threadpool_info()) or 1
+    except Exception:
+        cores = os.cpu_count()
+    sample = f"1 k-point x 2 spins x {nbs} bands of the 96^3 oxide workload per step (full pass)"
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 2), "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": WORKLOAD}, "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores,
+                                                                         "kind": "oracle", "sample": sample},
+                      "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--grid", type=int, default=96)
+    ap.add_argument("--nkgrid", type=int, default=2)
+    ap.add_argument("--nbands", type=int, default=256)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,177 @@
+/*
+ * dftu.h -- C ABI of the GB300 Hubbard-projector library (libdftu.so).
+ *
+ * The library implements the data-parallel hot path of self-consistent DFT+U (ACBN0) on a
+ * real-space grid, after Tancogne-Dejean, Oliveira and Rubio, "Self-consistent DFT+U method for
+ * real-space time-dependent density functional theory calculations":
+ *
+ *   dftu_setup_atoms   spherical sub-grids and localised orbitals           Sec. II, Fig. 1
+ *   dftu_project       p = <phi_{I,m,k} | psi_{n,k}>                         inside Eqs. (4), (6)
+ *   dftu_occupations   n^{I,sigma}_{mm'}, Nbar, Pbar                         Eqs. (4), (8), (9), (A2), (B3)
+ *   dftu_acbn0_uj      Ubar, Jbar, U_eff, E_U and the potential V            Eqs. (3), (6), (10), (11), (A5), (B5), (B6)
+ *   dftu_apply         psi += c * sum_{mm'} V_{mm'} |phi_m><phi_m'|psi>      Eq. (6)
+ *
+ * Conventions shared by every entry point
+ *   - Units are Hartree atomic units (bohr, Hartree).  U, J and E_U are returned in Hartree.
+ *   - Grid point (i,j,k) has linear index i + n0*(j + n1*k) and position (i*h0+o0, j*h1+o1, k*h2+o2).
+ *   - States are caller-owned DEVICE arrays of interleaved complex numbers (complex128 for
+ *     DFTU_C128, complex64 for DFTU_C64).  Layout, with ld_band >= npts elements between bands:
+ *       collinear / unpolarised: psi[k][spin][band][ld_band]  (spin extent 2 or 1)
+ *       non-collinear:           psi[k][band][component][ld_band] (component extent 2)
+ *   - psi is the full Bloch function on the cell.  A sphere point at unfolded position r_u folds
+ *     to r_w = r_u - T; the gather multiplies psi(r_w) by exp(+i k.T), the scatter by exp(-i k.T).
+ *   - Occupation matrices are reported as the paper's n_{mm'} = sum w f <psi|phi_m><phi_m'|psi>.
+ *     Internally the library holds rho = n^T and applies V = U_eff (1/2 - rho): with complex
+ *     projections this is the gradient of E_U (the printed V = U_eff (1/2 - n) is its transpose).
+ *   - Spin-unpolarised runs hold one channel whose occupations are per spin; spin sums count it twice.
+ *   - Every compute call is asynchronous on the given stream (a cudaStream_t passed as void*;
+ *     NULL = legacy default stream) and allocates nothing: all device memory is allocated by
+ *     dftu_create and dftu_setup_atoms.  Errors detected on the device (non-finite projections,
+ *     zero ACBN0 denominators) set bits of a device status word read by dftu_sync_status.
+ *   - Return value: DFTU_OK, or an error code; dftu_last_error() gives a message.  On an argument
+ *     error nothing is launched and the handle is unchanged.
+ */
+#ifndef DFTU_H
+#define DFTU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dftu_ctx* dftu_handle;
+typedef void* dftu_stream; /* a cudaStream_t */
+
+typedef enum {
+    DFTU_OK = 0,
+    DFTU_ERR_INVALID_ARG = 1,  /* bad argument; nothing was launched */
+    DFTU_ERR_NOT_READY = 2,    /* a prerequisite call is missing (setup, Coulomb, project, ...) */
+    DFTU_ERR_ALLOC = 3,        /* device or host allocation failed */
+    DFTU_ERR_CUDA = 4,         /* a CUDA runtime or cuFFT call failed */
+    DFTU_ERR_NONFINITE = 5,    /* a projection was NaN or infinite (device status) */
+    DFTU_ERR_ZERO_DENOM = 6,   /* an ACBN0 denominator was < 1e-14: U = J = 0 for that atom (warning) */
+    DFTU_ERR_TIMEOUT = 7       /* a bounded device-side wait gave up (device status) */
+} dftu_status;
+
+/* Orthorhombic grid. periodic = 1: the cell repeats; 0: isolated box (sphere points outside it are dropped). */
+typedef struct { int n[3]; double h[3]; double origin[3]; int periodic; } dftu_grid;
+
+/* A correlated atom: one shell of angular momentum l (0..3, M = 2l+1 orbitals) on a sphere of the
+ * given radius (bohr).  species indexes the radial table and the Coulomb integrals; Nbar (Eq. 9)
+ * sums over all atoms of the same species. */
+typedef struct { double pos[3]; int species; int l; double radius; } dftu_atom;
+
+/* Radial function R(r) of a species' localised orbital on the uniform grid r_i = i*dr, i < nr (nr >= 4).
+ * Host pointer, copied during dftu_setup_atoms.  The library interpolates it with 4-point Lagrange
+ * polynomials (nodes a..a+3, a = clamp(floor(r/dr)-1, 0, nr-4)) and takes R = 0 at and beyond r_{nr-1}. */
+typedef struct { int nr; double dr; const double* R; } dftu_radial;
+
+typedef enum { DFTU_C128 = 0, DFTU_C64 = 1 } dftu_prec;
+typedef enum { DFTU_COLLINEAR = 0, DFTU_UNPOLARIZED = 1, DFTU_NONCOLLINEAR = 2 } dftu_spin;
+
+/* Arithmetic used for DFTU_C128 states.
+ *   DFTU_F64_PAIR   (default) products and sums carried as pairs of FP32 numbers on the FP32 pipes,
+ *                   about 2^-44 relative; needed because this GPU's FP64 pipe is ~1/70 of its FP32 rate.
+ *   DFTU_F64_NATIVE plain FP64 fused multiply-adds. */
+typedef enum { DFTU_F64_PAIR = 0, DFTU_F64_NATIVE = 1 } dftu_f64_mode;
+
+/* Create a context on CUDA device `device`.
+ *   kvec  host [nk][3] Cartesian k-points, 1/bohr (copied).
+ *   wk    host [nk] k-point weights (copied; they should sum to 1).
+ *   max_bands  upper bound on the nbands of later calls; sizes the internal buffers.
+ * Ownership: the handle owns everything it allocates; release with dftu_destroy. */
+dftu_status dftu_create(dftu_handle* out, const dftu_grid* grid, int nk, const double* kvec,
+                        const double* wk, dftu_spin spin, int max_bands, int device);
+
+/* Build the spherical sub-grid of every atom (Sec. II, Fig. 1): grid points with
+ * (dx*dx + dy*dy) + dz*dz <= R*R in FP64 round-to-nearest without fused multiply-add,
+ * dx = (i*h + origin) - X over unfolded integer coordinates, folded into the cell with their
+ * lattice image T (|T| <= 2 cells per axis).  Sample phi = R(|d|) Y_lm(d) (real harmonics,
+ * m = -l..l: p = y,z,x; d = xy,yz,3z^2-r^2,xz,x^2-y^2) and orthonormalise each atom's orbitals
+ * with S^{-1/2}, S = dV phi^T phi (Sec. III assumes an orthogonal basis on each atom).
+ * atoms, radials: host arrays (copied).  npts_out: host [natoms] sphere point counts, or NULL.
+ * Blocking (synchronises the device).  May be called once per handle. */
+dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, int nspecies,
+                             const dftu_radial* radials, int* npts_out);
+
+/* Copy atom `atom`'s sphere map to host arrays in canonical order (z outer, y, x inner, ascending
+ * unfolded coordinates): idx_out [npts] wrapped linear index, image_out [npts][3] lattice image in
+ * cells, phi_out [npts][M] orthonormal orbitals (any of the three may be NULL).  Blocking. */
+dftu_status dftu_get_sphere(dftu_handle h, int atom, int32_t* idx_out, int32_t* image_out, double* phi_out);
+
+/* Coulomb integrals (mm'|m''m''') of a species (Sec. III; definition Eq. B2), computed on the GPU
+ * from the orbitals of the species' first atom: pair densities on a zero-padded box of edge
+ * >= 2R + Rc (2,3,5-smooth sizes), Rc = 2R + 2 max(h), FFT Poisson solve with the truncated kernel
+ * 4 pi (1 - cos(G Rc)) / G^2 (2 pi Rc^2 at G = 0), then dV sum phi_m phi_m' v_{m''m'''}.
+ * The result is stored in the handle for dftu_acbn0_uj; V_out: host [M^4] Hartree, or NULL.  Blocking. */
+dftu_status dftu_coulomb_integrals(dftu_handle h, int species, double* V_out);
+
+/* Set a species' Coulomb integrals from host memory instead: V [M][M][M][M] Hartree (copied). */
+dftu_status dftu_set_coulomb(dftu_handle h, int species, const double* V);
+
+/* Fixed-U DFT+U for one atom (Sec. II): dftu_acbn0_uj then uses these U, J (Hartree) for it
+ * instead of evaluating ACBN0.  U = J = NaN returns the atom to ACBN0. */
+dftu_status dftu_set_u(dftu_handle h, int atom, double U, double J);
+
+/* Choose the arithmetic for DFTU_C128 states (see dftu_f64_mode). */
+dftu_status dftu_set_f64_mode(dftu_handle h, dftu_f64_mode mode);
+
+/* Projections p^{k,s}_{I,m,n} = dV sum_j phi_{I,m}(j) exp(+i k.T_j) psi_{k,s,n}(idx_j) of the first
+ * nbands bands (nbands <= max_bands) of psi (device, layout above) onto every atom's orbitals.
+ * DFTU_C64 states are multiplied by FP32 orbitals with an FP32 low-part correction, summed in FP32
+ * within a point tile and in FP64 across tiles; DFTU_C128 follows dftu_set_f64_mode.
+ * The result stays on the device for the calls below. */
+dftu_status dftu_project(dftu_handle h, const void* psi, dftu_prec prec, int nbands, int64_t ld_band,
+                         dftu_stream stream);
+
+/* Occupations from the last projections, Eq. (4), with Nbar (Eq. 9: sum over the atoms of the same
+ * species and all m of |p|^2; non-collinear: also over both spinor components) and Pbar (Eq. 8).
+ * f: device FP64 occupations, [nk][spin][nbands] (non-collinear [nk][nbands]), per spin. */
+dftu_status dftu_occupations(dftu_handle h, const double* f, dftu_stream stream);
+
+/* Per atom: ACBN0 Ubar and Jbar (Eqs. 10-11 collinear, B5-B6 non-collinear; numerators with
+ * Pbar_{mm'} Pbar_{m''m'''} as in Eq. 7, denominators with N_m = n_mm), or the fixed U, J of
+ * dftu_set_u; then U_eff = U - J, E_U (Eq. 3 / A5) and V = U_eff (1/2 - n^T) (Eq. 6).
+ * A denominator < 1e-14 gives U = J = 0 and sets DFTU_ERR_ZERO_DENOM in the device status. */
+dftu_status dftu_acbn0_uj(dftu_handle h, dftu_stream stream);
+
+/* psi_out(idx_j) += c exp(-i k.T_j) sum_m phi_m(j) (V p)_m for every atom and sphere point (Eq. 6),
+ * with p from the last dftu_project (which may have read a different array) and V from the last
+ * dftu_acbn0_uj.  coef: device pointer to one complex FP64 number c, or NULL for c = 1.
+ * Points shared by several spheres receive every contribution, in a fixed order. */
+dftu_status dftu_apply(dftu_handle h, void* psi_out, dftu_prec prec, int nbands, int64_t ld_band,
+                       const double* coef, dftu_stream stream);
+
+/* Results to host memory (blocking on stream).  Any pointer may be NULL.
+ *   n_out     [atom][spin][M][M] interleaved complex (paper's n, Eq. 4); non-collinear [atom][2M][2M]
+ *             with index (component*M + m); atoms packed one after another with their own M.
+ *   U, J, EU_atom  [natoms] Hartree;  EU_total: sum over atoms (Hartree). */
+dftu_status dftu_get_results(dftu_handle h, double* n_out, double* U, double* J, double* EU_atom,
+                             double* EU_total, dftu_stream stream);
+
+/* Pbar (Eq. 8) in the same layout as n_out, and Nbar [nk][spin][nbands][nspecies] (non-collinear
+ * [nk][nbands][nspecies]) to host memory (blocking). */
+dftu_status dftu_get_renormalized(dftu_handle h, double* Pbar_out, double* Nbar_out, dftu_stream stream);
+
+/* Last projections to host: [nk][spin or component][nbands][sum_I M_I] interleaved complex (blocking). */
+dftu_status dftu_get_projections(dftu_handle h, double* p_out, dftu_stream stream);
+
+/* Number of orbitals summed over atoms (sum_I M_I), and the number of sphere points of an atom. */
+int dftu_total_orbitals(dftu_handle h);
+int dftu_atom_points(dftu_handle h, int atom);
+
+/* Synchronise the stream of the last compute call and return the device status word as a
+ * dftu_status (first set of: NONFINITE, TIMEOUT, ZERO_DENOM), clearing it. */
+dftu_status dftu_sync_status(dftu_handle h);
+
+/* Message of the last error on this handle (never NULL; valid until the next call). */
+const char* dftu_last_error(dftu_handle h);
+
+/* Release everything the handle owns.  NULL is ignored. */
+void dftu_destroy(dftu_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DFTU_H */

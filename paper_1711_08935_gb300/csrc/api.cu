@@ -1,0 +1,701 @@
+// C ABI entry points of libdftu.so (declared in include/dftu.h): argument checks, the one-off
+// geometry set-up (sphere membership on the device, point ordering, tiling and apply colouring on the
+// host), buffer ownership, and the asynchronous launches of the hot path.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "dftu_internal.cuh"
+
+using namespace dftu;
+
+namespace {
+
+struct Guard {   // sets the context's device for the duration of an entry point
+    int prev = -1;
+    explicit Guard(int dev) { cudaGetDevice(&prev); cudaSetDevice(dev); }
+    ~Guard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
+dftu_status fail(Ctx* c, dftu_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+dftu_status cuda_fail(Ctx* c, cudaError_t e, const char* where) {
+    return fail(c, e == cudaErrorMemoryAllocation ? DFTU_ERR_ALLOC : DFTU_ERR_CUDA,
+                std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+template <class T>
+cudaError_t dalloc(Ctx* c, T** p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T));
+    if (e == cudaSuccess) c->allocs.push_back(*p);
+    return e;
+}
+
+template <class T>
+cudaError_t upload(Ctx* c, T** p, const std::vector<T>& h) {
+    cudaError_t e = dalloc(c, p, h.size());
+    if (e != cudaSuccess) return e;
+    if (!h.empty()) e = cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+int64_t floor_div64(int64_t a, int64_t n) {
+    int64_t q = a / n;
+    return (a % n != 0 && ((a < 0) != (n < 0))) ? q - 1 : q;
+}
+
+bool valid_stride_args(Ctx* c, int nbands, int64_t ld) {
+    return nbands >= 1 && nbands <= c->max_bands && ld >= (int64_t)c->grid.n[0] * c->grid.n[1] * c->grid.n[2];
+}
+
+void strides(const Ctx* c, int nbands, int64_t ld, int64_t& sk, int64_t& ss, int64_t& sn) {
+    if (c->spin == DFTU_NONCOLLINEAR) {
+        ss = ld;
+        sn = 2 * ld;
+        sk = (int64_t)nbands * 2 * ld;
+    } else {
+        sn = ld;
+        ss = (int64_t)nbands * ld;
+        sk = (int64_t)c->ns * nbands * ld;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+dftu_status dftu_create(dftu_handle* out, const dftu_grid* grid, int nk, const double* kvec, const double* wk,
+                        dftu_spin spin, int max_bands, int device) {
+    if (!out) return DFTU_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!grid || nk < 1 || !kvec || !wk || max_bands < 1 ||
+        (spin != DFTU_COLLINEAR && spin != DFTU_UNPOLARIZED && spin != DFTU_NONCOLLINEAR))
+        return DFTU_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (grid->n[a] < 1 || !(grid->h[a] > 0.0) || !std::isfinite(grid->origin[a])) return DFTU_ERR_INVALID_ARG;
+    if ((int64_t)grid->n[0] * grid->n[1] * grid->n[2] >= (int64_t)1 << 31) return DFTU_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return DFTU_ERR_INVALID_ARG;
+    Ctx* c = new (std::nothrow) Ctx();
+    if (!c) return DFTU_ERR_ALLOC;
+    c->device = device;
+    c->grid = *grid;
+    c->nk = nk;
+    c->spin = spin;
+    c->ns = (spin == DFTU_UNPOLARIZED) ? 1 : 2;
+    c->max_bands = max_bands;
+    c->kvec.assign(kvec, kvec + 3 * nk);
+    c->wk.assign(wk, wk + nk);
+    Guard g(device);
+    View& v = c->v;
+    v.n0 = grid->n[0]; v.n1 = grid->n[1]; v.n2 = grid->n[2];
+    v.h0 = grid->h[0]; v.h1 = grid->h[1]; v.h2 = grid->h[2];
+    v.o0 = grid->origin[0]; v.o1 = grid->origin[1]; v.o2 = grid->origin[2];
+    v.periodic = grid->periodic ? 1 : 0;
+    v.dV = grid->h[0] * grid->h[1] * grid->h[2];
+    v.nk = nk;
+    v.ns = c->ns;
+    v.noncollinear = spin == DFTU_NONCOLLINEAR;
+    v.max_bands = max_bands;
+    int* st = nullptr;
+    double* one = nullptr;
+    cudaError_t e = upload(c, const_cast<double**>(&v.kvec), c->kvec);
+    if (e == cudaSuccess) e = upload(c, const_cast<double**>(&v.wk), c->wk);
+    if (e == cudaSuccess) e = dalloc(c, &st, 1);
+    if (e == cudaSuccess) e = cudaMemset(st, 0, sizeof(int));
+    if (e == cudaSuccess) e = upload(c, &one, std::vector<double>{1.0, 0.0});
+    if (e != cudaSuccess) {
+        for (void* p : c->allocs) cudaFree(p);
+        delete c;
+        return e == cudaErrorMemoryAllocation ? DFTU_ERR_ALLOC : DFTU_ERR_CUDA;
+    }
+    v.status = st;
+    c->d_coef_one = one;
+    *out = reinterpret_cast<dftu_handle>(c);
+    return DFTU_OK;
+}
+
+dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, int nspecies, const dftu_radial* radials,
+                             int* npts_out) {
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c) return DFTU_ERR_INVALID_ARG;
+    if (c->atoms_ready) return fail(c, DFTU_ERR_INVALID_ARG, "setup_atoms: already called on this handle");
+    if (natoms < 1 || !atoms || nspecies < 1 || !radials) return fail(c, DFTU_ERR_INVALID_ARG, "setup_atoms: bad counts or null arrays");
+    std::vector<int> spM(nspecies, -1);
+    for (int s = 0; s < nspecies; ++s)
+        if (radials[s].nr < 4 || !(radials[s].dr > 0.0) || !radials[s].R)
+            return fail(c, DFTU_ERR_INVALID_ARG, "setup_atoms: radial table needs nr >= 4, dr > 0 and data");
+    const dftu_grid& G = c->grid;
+    for (int a = 0; a < natoms; ++a) {
+        const dftu_atom& at = atoms[a];
+        if (at.species < 0 || at.species >= nspecies || at.l < 0 || at.l > 3 || !(at.radius > 0.0) ||
+            !std::isfinite(at.pos[0]) || !std::isfinite(at.pos[1]) || !std::isfinite(at.pos[2]))
+            return fail(c, DFTU_ERR_INVALID_ARG, "setup_atoms: atom " + std::to_string(a) + " has a bad species, l, radius or position");
+        int M = 2 * at.l + 1;
+        if (spM[at.species] >= 0 && spM[at.species] != M)
+            return fail(c, DFTU_ERR_INVALID_ARG, "setup_atoms: atoms of one species must share l");
+        spM[at.species] = M;
+    }
+    for (int s = 0; s < nspecies; ++s)
+        if (spM[s] < 0) spM[s] = 1;
+    Guard g(c->device);
+    View& v = c->v;
+    // ---- bounding boxes and device membership flags ----
+    std::vector<int> box_lo(3 * natoms), box_dim(3 * natoms);
+    std::vector<int64_t> box_off(natoms + 1, 0);
+    std::vector<double> pos(3 * natoms), rad(natoms);
+    for (int a = 0; a < natoms; ++a) {
+        const dftu_atom& at = atoms[a];
+        rad[a] = at.radius;
+        for (int d = 0; d < 3; ++d) {
+            pos[3 * a + d] = at.pos[d];
+            double lo = std::floor((at.pos[d] - at.radius - G.origin[d]) / G.h[d]) - 1;
+            double hi = std::ceil((at.pos[d] + at.radius - G.origin[d]) / G.h[d]) + 1;
+            if (std::fabs(lo) > 1e8 || std::fabs(hi) > 1e8)
+                return fail(c, DFTU_ERR_INVALID_ARG, "setup_atoms: sphere too far from the grid");
+            box_lo[3 * a + d] = (int)lo;
+            box_dim[3 * a + d] = (int)(hi - lo) + 1;
+            if (G.periodic) {
+                int64_t tlo = floor_div64((int64_t)lo, G.n[d]), thi = floor_div64((int64_t)hi, G.n[d]);
+                if (tlo < -IMG_RANGE || thi > IMG_RANGE)
+                    return fail(c, DFTU_ERR_INVALID_ARG, "setup_atoms: a sphere reaches beyond two periodic images");
+            }
+        }
+        box_off[a + 1] = box_off[a] + (int64_t)box_dim[3 * a] * box_dim[3 * a + 1] * box_dim[3 * a + 2];
+    }
+    const int64_t nbox = box_off[natoms];
+    std::vector<signed char> flags(nbox);
+    {
+        double *dpos, *drad;
+        int *dlo, *ddim;
+        int64_t* doff;
+        signed char* dflags;
+        cudaError_t e = cudaMalloc(&dpos, pos.size() * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&drad, rad.size() * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&dlo, box_lo.size() * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&ddim, box_dim.size() * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&doff, box_off.size() * sizeof(int64_t));
+        if (e == cudaSuccess) e = cudaMalloc(&dflags, (size_t)nbox);
+        if (e != cudaSuccess) return cuda_fail(c, e, "setup_atoms: temporary allocation");
+        cudaMemcpy(dpos, pos.data(), pos.size() * sizeof(double), cudaMemcpyHostToDevice);
+        cudaMemcpy(drad, rad.data(), rad.size() * sizeof(double), cudaMemcpyHostToDevice);
+        cudaMemcpy(dlo, box_lo.data(), box_lo.size() * sizeof(int), cudaMemcpyHostToDevice);
+        cudaMemcpy(ddim, box_dim.data(), box_dim.size() * sizeof(int), cudaMemcpyHostToDevice);
+        cudaMemcpy(doff, box_off.data(), box_off.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+        e = launch_sphere_flags(v, dpos, drad, dlo, ddim, doff, natoms, nbox, dflags, 0);
+        if (e == cudaSuccess) e = cudaMemcpy(flags.data(), dflags, (size_t)nbox, cudaMemcpyDeviceToHost);
+        cudaFree(dpos); cudaFree(drad); cudaFree(dlo); cudaFree(ddim); cudaFree(doff); cudaFree(dflags);
+        if (e != cudaSuccess) return cuda_fail(c, e, "setup_atoms: sphere membership");
+    }
+    // ---- point order: atom-major, then image segment, then canonical (z, y, x) ----
+    c->atoms.assign(atoms, atoms + natoms);
+    c->nspecies = nspecies;
+    c->species_M = spM;
+    c->M.resize(natoms); c->moff.resize(natoms); c->mat_off.resize(natoms); c->npts.resize(natoms);
+    c->canon_to_gpu.assign(natoms, {});
+    c->atom_p0.resize(natoms); c->atom_phi0.resize(natoms);
+    c->atom_umin.assign(natoms, std::vector<int>(3, 0));
+    std::vector<int> pt_idx, pt_u, seg_T;
+    std::vector<int> seg_atom;
+    std::vector<std::vector<int>> seg_points;   // wrapped indices per segment (for colouring)
+    c->tiles.clear();
+    int MT = 0, TM = 0, mat = 0;
+    int64_t phi_off = 0;
+    const int64_t n0 = G.n[0], n1 = G.n[1], n2 = G.n[2];
+    for (int a = 0; a < natoms; ++a) {
+        const int M = 2 * atoms[a].l + 1;
+        c->M[a] = M;
+        c->moff[a] = MT;
+        MT += M;
+        c->mat_off[a] = mat;
+        mat += (c->spin == DFTU_NONCOLLINEAR) ? 4 * M * M : c->ns * M * M;
+        int bx = box_dim[3 * a], by = box_dim[3 * a + 1];
+        std::vector<std::vector<int64_t>> by_img(NIMG);
+        int64_t nin = 0;
+        for (int64_t b = 0; b < box_off[a + 1] - box_off[a]; ++b) {
+            signed char f = flags[box_off[a] + b];
+            if (f < 0) continue;
+            by_img[f].push_back(b);
+            ++nin;
+        }
+        if (nin == 0) return fail(c, DFTU_ERR_INVALID_ARG, "setup_atoms: atom " + std::to_string(a) + " has no grid point in its sphere");
+        if (nin > (int64_t)1 << 30) return fail(c, DFTU_ERR_INVALID_ARG, "setup_atoms: sphere too large");
+        c->npts[a] = (int)nin;
+        c->atom_p0[a] = (int64_t)pt_idx.size();
+        c->atom_phi0[a] = phi_off;
+        // canonical rank of every box point inside the sphere
+        std::vector<int64_t> canon_rank(box_off[a + 1] - box_off[a], -1);
+        {
+            int64_t r = 0;
+            for (int64_t b = 0; b < box_off[a + 1] - box_off[a]; ++b)
+                if (flags[box_off[a] + b] >= 0) canon_rank[b] = r++;
+        }
+        c->canon_to_gpu[a].assign(nin, 0);
+        int umin[3] = {1 << 30, 1 << 30, 1 << 30};
+        int local = 0;
+        for (int img = 0; img < NIMG; ++img) {
+            const auto& L = by_img[img];
+            if (L.empty()) continue;
+            int segid = (int)seg_atom.size();
+            seg_atom.push_back(a);
+            int tx = img % 5 - IMG_RANGE, ty = (img / 5) % 5 - IMG_RANGE, tz = img / 25 - IMG_RANGE;
+            if (!G.periodic) tx = ty = tz = 0;
+            seg_T.push_back(tx); seg_T.push_back(ty); seg_T.push_back(tz);
+            seg_points.emplace_back();
+            int64_t first = (int64_t)pt_idx.size();
+            for (int64_t b : L) {
+                int ix = box_lo[3 * a] + (int)(b % bx);
+                int jy = box_lo[3 * a + 1] + (int)((b / bx) % by);
+                int kz = box_lo[3 * a + 2] + (int)(b / ((int64_t)bx * by));
+                int64_t wx = ix - (int64_t)tx * n0, wy = jy - (int64_t)ty * n1, wz = kz - (int64_t)tz * n2;
+                int idx = (int)(wx + n0 * (wy + n1 * wz));
+                pt_idx.push_back(idx);
+                pt_u.push_back(ix); pt_u.push_back(jy); pt_u.push_back(kz);
+                umin[0] = std::min(umin[0], ix); umin[1] = std::min(umin[1], jy); umin[2] = std::min(umin[2], kz);
+                seg_points.back().push_back(idx);
+                c->canon_to_gpu[a][canon_rank[b]] = local++;
+            }
+            int64_t len = (int64_t)pt_idx.size() - first;
+            int64_t nt = (len + TILE - 1) / TILE;
+            int64_t base = len / nt, rem = len % nt, at = first;
+            for (int64_t q = 0; q < nt; ++q) {
+                int np = (int)(base + (q < rem ? 1 : 0));
+                Tile t{};
+                t.atom = a; t.M = M; t.seg = segid; t.np = np; t.p0 = at;
+                t.phi0 = phi_off + (at - c->atom_p0[a]) * M;
+                t.moff = TM;
+                t.color = 0;
+                TM += M;
+                c->tiles.push_back(t);
+                at += np;
+            }
+        }
+        for (int d = 0; d < 3; ++d) c->atom_umin[a][d] = umin[d];
+        phi_off += nin * M;
+    }
+    c->MT = MT;
+    c->TM = TM;
+    c->mat_total = mat;
+    c->S = (int64_t)pt_idx.size();
+    c->phi_total = phi_off;
+    // ---- apply colouring: greedy, segments sharing a grid point get different colours ----
+    const int nseg = (int)seg_atom.size();
+    std::vector<int> seg_color(nseg, -1);
+    {
+        const int64_t npts = n0 * n1 * n2;
+        std::vector<std::vector<unsigned char>> used;
+        for (int s = 0; s < nseg; ++s) {
+            int col = 0;
+            for (;; ++col) {
+                if (col == (int)used.size()) used.emplace_back(npts, 0);
+                bool clash = false;
+                for (int idx : seg_points[s])
+                    if (used[col][idx]) { clash = true; break; }
+                if (!clash) break;
+                if (col >= 255) return fail(c, DFTU_ERR_INVALID_ARG, "setup_atoms: too many overlapping spheres");
+            }
+            seg_color[s] = col;
+            for (int idx : seg_points[s]) used[col][idx] = 1;
+        }
+        int ncol = used.size();
+        c->color_beg.assign(ncol + 1, 0);
+        c->color_order.clear();
+        for (int col = 0; col < ncol; ++col) {
+            c->color_beg[col] = (int)c->color_order.size();
+            for (size_t t = 0; t < c->tiles.size(); ++t)
+                if (seg_color[c->tiles[t].seg] == col) {
+                    c->tiles[t].color = col;
+                    c->color_order.push_back((int)t);
+                }
+        }
+        c->color_beg[ncol] = (int)c->color_order.size();
+    }
+    // ---- per-atom tile ranges, species data, radial tables ----
+    std::vector<int> tbeg(natoms, 0), tend(natoms, 0);
+    for (size_t t = 0; t < c->tiles.size(); ++t) {
+        int a = c->tiles[t].atom;
+        if (t == 0 || c->tiles[t - 1].atom != a) tbeg[a] = (int)t;
+        tend[a] = (int)t + 1;
+    }
+    std::vector<int> aM(c->M), asp(natoms), amoff(c->moff), amat(c->mat_off);
+    for (int a = 0; a < natoms; ++a) asp[a] = atoms[a].species;
+    c->coul_off.assign(nspecies, 0);
+    int coul_total = 0;
+    for (int s = 0; s < nspecies; ++s) { c->coul_off[s] = coul_total; coul_total += spM[s] * spM[s] * spM[s] * spM[s]; }
+    std::vector<double> rtab;
+    std::vector<int> roff(nspecies), rnr(nspecies);
+    std::vector<double> rdr(nspecies);
+    for (int s = 0; s < nspecies; ++s) {
+        roff[s] = (int)rtab.size();
+        rnr[s] = radials[s].nr;
+        rdr[s] = radials[s].dr;
+        rtab.insert(rtab.end(), radials[s].R, radials[s].R + radials[s].nr);
+    }
+    std::vector<double> nanv(natoms, std::nan(""));
+    cudaError_t e = cudaSuccess;
+    Tile* dt = nullptr;
+    int *d_idx, *d_u, *d_segT, *d_aM, *d_asp, *d_amoff, *d_amat, *d_tb, *d_te, *d_coff, *d_spM, *d_cset;
+    double *d_pos, *d_rad, *d_rtab, *d_rdr, *d_fu, *d_fj, *d_coul;
+    int *d_roff, *d_rnr;
+    double2* d_segph;
+    e = upload(c, &dt, c->tiles);
+    if (e == cudaSuccess) e = upload(c, &d_idx, pt_idx);
+    if (e == cudaSuccess) e = upload(c, &d_u, pt_u);
+    if (e == cudaSuccess) e = upload(c, &d_segT, seg_T);
+    if (e == cudaSuccess) e = dalloc(c, &d_segph, (size_t)nseg * c->nk);
+    if (e == cudaSuccess) e = upload(c, &d_aM, aM);
+    if (e == cudaSuccess) e = upload(c, &d_asp, asp);
+    if (e == cudaSuccess) e = upload(c, &d_amoff, amoff);
+    if (e == cudaSuccess) e = upload(c, &d_amat, amat);
+    if (e == cudaSuccess) e = upload(c, &d_tb, tbeg);
+    if (e == cudaSuccess) e = upload(c, &d_te, tend);
+    if (e == cudaSuccess) e = upload(c, &d_coff, c->coul_off);
+    if (e == cudaSuccess) e = upload(c, &d_spM, spM);
+    if (e == cudaSuccess) e = upload(c, &d_pos, pos);
+    if (e == cudaSuccess) e = upload(c, &d_rad, rad);
+    if (e == cudaSuccess) e = upload(c, &d_rtab, rtab);
+    if (e == cudaSuccess) e = upload(c, &d_roff, roff);
+    if (e == cudaSuccess) e = upload(c, &d_rnr, rnr);
+    if (e == cudaSuccess) e = upload(c, &d_rdr, rdr);
+    if (e == cudaSuccess) e = upload(c, &d_fu, nanv);
+    if (e == cudaSuccess) e = upload(c, &d_fj, nanv);
+    if (e == cudaSuccess) e = upload(c, &d_cset, std::vector<int>(nspecies, 0));
+    if (e == cudaSuccess) e = dalloc(c, &d_coul, (size_t)coul_total);
+    if (e == cudaSuccess) e = upload(c, &c->d_color_order, c->color_order);
+    if (e != cudaSuccess) return cuda_fail(c, e, "setup_atoms: upload");
+    v.natoms = natoms; v.nspecies = nspecies; v.MT = MT; v.TM = TM; v.ntiles = (int)c->tiles.size(); v.nseg = nseg;
+    v.atom_pos = d_pos; v.atom_rad = d_rad; v.atom_M = d_aM; v.atom_species = d_asp; v.atom_moff = d_amoff;
+    v.atom_mat_off = d_amat; v.atom_tile_beg = d_tb; v.atom_tile_end = d_te; v.species_coul_off = d_coff; v.species_M = d_spM;
+    v.tiles = dt; v.pt_idx = d_idx; v.pt_u = d_u; v.seg_T = d_segT; v.seg_phase = d_segph;
+    v.coul = d_coul; v.coul_set = d_cset; v.fixU = d_fu; v.fixJ = d_fj;
+    // ---- work buffers ----
+    const int rowsP = c->nk * c->ns;
+    const int rowsN = (c->spin == DFTU_NONCOLLINEAR) ? c->nk : c->nk * c->ns;
+    e = dalloc(c, &v.phi64, (size_t)phi_off);
+    if (e == cudaSuccess) e = dalloc(c, &v.phi_hi, (size_t)phi_off);
+    if (e == cudaSuccess) e = dalloc(c, &v.phi_lo, (size_t)phi_off);
+    if (e == cudaSuccess) e = dalloc(c, &v.p, (size_t)rowsP * c->max_bands * MT);
+    if (e == cudaSuccess) e = dalloc(c, &v.part, (size_t)rowsP * c->max_bands * TM);
+    if (e == cudaSuccess) e = dalloc(c, &v.nbar, (size_t)rowsN * c->max_bands * nspecies);
+    if (e == cudaSuccess) e = dalloc(c, &v.rho, (size_t)mat);
+    if (e == cudaSuccess) e = dalloc(c, &v.pbar, (size_t)mat);
+    if (e == cudaSuccess) e = dalloc(c, &v.V, (size_t)mat);
+    if (e == cudaSuccess) e = dalloc(c, &v.U, (size_t)natoms);
+    if (e == cudaSuccess) e = dalloc(c, &v.J, (size_t)natoms);
+    if (e == cudaSuccess) e = dalloc(c, &v.E, (size_t)natoms);
+    if (e == cudaSuccess) e = dalloc(c, &v.Etot, 1);
+    double* work = nullptr;
+    if (e == cudaSuccess) e = dalloc(c, &work, (size_t)natoms * MAXM * MAXM);
+    if (e != cudaSuccess) return cuda_fail(c, e, "setup_atoms: work buffers");
+    // ---- phases, orbitals, Loewdin ----
+    e = launch_seg_phases(v, 0);
+    if (e == cudaSuccess) e = launch_orbitals(v, d_rtab, d_roff, d_rnr, d_rdr, 0);
+    if (e == cudaSuccess) e = launch_lowdin(v, work, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(c, e, "setup_atoms: orbitals");
+    if (npts_out)
+        for (int a = 0; a < natoms; ++a) npts_out[a] = c->npts[a];
+    c->atoms_ready = true;
+    return DFTU_OK;
+}
+
+dftu_status dftu_get_sphere(dftu_handle h, int atom, int32_t* idx_out, int32_t* image_out, double* phi_out) {
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c) return DFTU_ERR_INVALID_ARG;
+    if (!c->atoms_ready) return fail(c, DFTU_ERR_NOT_READY, "get_sphere: call dftu_setup_atoms first");
+    if (atom < 0 || atom >= (int)c->atoms.size()) return fail(c, DFTU_ERR_INVALID_ARG, "get_sphere: bad atom");
+    Guard g(c->device);
+    const int n = c->npts[atom], M = c->M[atom];
+    std::vector<int> idx(n), u(3 * (size_t)n);
+    std::vector<double> phi((size_t)n * M);
+    cudaError_t e = cudaMemcpy(idx.data(), c->v.pt_idx + c->atom_p0[atom], n * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(u.data(), c->v.pt_u + 3 * c->atom_p0[atom], 3 * (size_t)n * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(phi.data(), c->v.phi64 + c->atom_phi0[atom], (size_t)n * M * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "get_sphere");
+    const int* nn = c->grid.n;
+    for (int r = 0; r < n; ++r) {
+        int gpos = c->canon_to_gpu[atom][r];
+        if (idx_out) idx_out[r] = idx[gpos];
+        if (image_out) {
+            int wx = idx[gpos] % nn[0], wy = (idx[gpos] / nn[0]) % nn[1], wz = idx[gpos] / (nn[0] * nn[1]);
+            image_out[3 * r] = (int)floor_div64(u[3 * gpos] - wx, nn[0]);
+            image_out[3 * r + 1] = (int)floor_div64(u[3 * gpos + 1] - wy, nn[1]);
+            image_out[3 * r + 2] = (int)floor_div64(u[3 * gpos + 2] - wz, nn[2]);
+        }
+        if (phi_out)
+            for (int m = 0; m < M; ++m) phi_out[(size_t)r * M + m] = phi[(size_t)gpos * M + m];
+    }
+    return DFTU_OK;
+}
+
+dftu_status dftu_coulomb_integrals(dftu_handle h, int species, double* V_out) {
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c) return DFTU_ERR_INVALID_ARG;
+    if (!c->atoms_ready) return fail(c, DFTU_ERR_NOT_READY, "coulomb_integrals: call dftu_setup_atoms first");
+    if (species < 0 || species >= c->nspecies) return fail(c, DFTU_ERR_INVALID_ARG, "coulomb_integrals: bad species");
+    int atom = -1;
+    for (size_t a = 0; a < c->atoms.size(); ++a)
+        if (c->atoms[a].species == species) { atom = (int)a; break; }
+    if (atom < 0) return fail(c, DFTU_ERR_INVALID_ARG, "coulomb_integrals: no atom of this species");
+    Guard g(c->device);
+    double* dst = const_cast<double*>(c->v.coul) + c->coul_off[species];
+    int rc = coulomb_atom(c->v, *c, atom, dst, c->err);
+    if (rc != DFTU_OK) return (dftu_status)rc;
+    int one = 1;
+    cudaError_t e = cudaMemcpy(const_cast<int*>(c->v.coul_set) + species, &one, sizeof(int), cudaMemcpyHostToDevice);
+    const int M = c->M[atom];
+    if (e == cudaSuccess && V_out) e = cudaMemcpy(V_out, dst, (size_t)M * M * M * M * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "coulomb_integrals");
+    return DFTU_OK;
+}
+
+dftu_status dftu_set_coulomb(dftu_handle h, int species, const double* V) {
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c) return DFTU_ERR_INVALID_ARG;
+    if (!c->atoms_ready) return fail(c, DFTU_ERR_NOT_READY, "set_coulomb: call dftu_setup_atoms first");
+    if (species < 0 || species >= c->nspecies || !V) return fail(c, DFTU_ERR_INVALID_ARG, "set_coulomb: bad species or null V");
+    Guard g(c->device);
+    const int M = c->species_M[species];
+    for (int e = 0; e < M * M * M * M; ++e)
+        if (!std::isfinite(V[e])) return fail(c, DFTU_ERR_INVALID_ARG, "set_coulomb: non-finite entry");
+    cudaError_t e = cudaMemcpy(const_cast<double*>(c->v.coul) + c->coul_off[species], V, (size_t)M * M * M * M * sizeof(double),
+                               cudaMemcpyHostToDevice);
+    int one = 1;
+    if (e == cudaSuccess) e = cudaMemcpy(const_cast<int*>(c->v.coul_set) + species, &one, sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set_coulomb");
+    return DFTU_OK;
+}
+
+dftu_status dftu_set_u(dftu_handle h, int atom, double U, double J) {
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c) return DFTU_ERR_INVALID_ARG;
+    if (!c->atoms_ready) return fail(c, DFTU_ERR_NOT_READY, "set_u: call dftu_setup_atoms first");
+    if (atom < 0 || atom >= (int)c->atoms.size()) return fail(c, DFTU_ERR_INVALID_ARG, "set_u: bad atom");
+    if (std::isnan(U) != std::isnan(J) || std::isinf(U) || std::isinf(J))
+        return fail(c, DFTU_ERR_INVALID_ARG, "set_u: U and J must both be finite, or both NaN");
+    Guard g(c->device);
+    cudaError_t e = cudaMemcpy(const_cast<double*>(c->v.fixU) + atom, &U, sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(const_cast<double*>(c->v.fixJ) + atom, &J, sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set_u");
+    return DFTU_OK;
+}
+
+dftu_status dftu_set_f64_mode(dftu_handle h, dftu_f64_mode mode) {
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c) return DFTU_ERR_INVALID_ARG;
+    if (mode != DFTU_F64_PAIR && mode != DFTU_F64_NATIVE) return fail(c, DFTU_ERR_INVALID_ARG, "set_f64_mode: bad mode");
+    c->f64_mode = mode;
+    return DFTU_OK;
+}
+
+dftu_status dftu_project(dftu_handle h, const void* psi, dftu_prec prec, int nbands, int64_t ld_band, dftu_stream stream) {
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c) return DFTU_ERR_INVALID_ARG;
+    if (!c->atoms_ready) return fail(c, DFTU_ERR_NOT_READY, "project: call dftu_setup_atoms first");
+    if (!psi || (prec != DFTU_C128 && prec != DFTU_C64) || !valid_stride_args(c, nbands, ld_band))
+        return fail(c, DFTU_ERR_INVALID_ARG, "project: null psi, bad precision, nbands outside [1, max_bands] or ld_band < npts");
+    Guard g(c->device);
+    int64_t sk, ss, sn;
+    strides(c, nbands, ld_band, sk, ss, sn);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_project(c->v, psi, prec, c->f64_mode, nbands, sk, ss, sn, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "project");
+    c->last_stream = st;
+    c->proj_ready = true;
+    c->proj_nbands = nbands;
+    return DFTU_OK;
+}
+
+dftu_status dftu_occupations(dftu_handle h, const double* f, dftu_stream stream) {
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c) return DFTU_ERR_INVALID_ARG;
+    if (!c->proj_ready) return fail(c, DFTU_ERR_NOT_READY, "occupations: call dftu_project first");
+    if (!f) return fail(c, DFTU_ERR_INVALID_ARG, "occupations: null f");
+    Guard g(c->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_nbar(c->v, c->proj_nbands, st);
+    if (e == cudaSuccess) e = launch_occupations(c->v, f, c->proj_nbands, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "occupations");
+    c->last_stream = st;
+    c->occ_ready = true;
+    return DFTU_OK;
+}
+
+dftu_status dftu_acbn0_uj(dftu_handle h, dftu_stream stream) {
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c) return DFTU_ERR_INVALID_ARG;
+    if (!c->occ_ready) return fail(c, DFTU_ERR_NOT_READY, "acbn0_uj: call dftu_occupations first");
+    Guard g(c->device);
+    std::vector<int> cset(c->nspecies);
+    std::vector<double> fu(c->atoms.size());
+    cudaError_t e = cudaMemcpy(cset.data(), c->v.coul_set, cset.size() * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(fu.data(), c->v.fixU, fu.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "acbn0_uj");
+    for (size_t a = 0; a < c->atoms.size(); ++a)
+        if (std::isnan(fu[a]) && !cset[c->atoms[a].species])
+            return fail(c, DFTU_ERR_NOT_READY, "acbn0_uj: Coulomb integrals of species " + std::to_string(c->atoms[a].species) +
+                                                   " not set (dftu_coulomb_integrals or dftu_set_coulomb), and no fixed U");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    e = launch_acbn0(c->v, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "acbn0_uj");
+    c->last_stream = st;
+    c->pot_ready = true;
+    return DFTU_OK;
+}
+
+dftu_status dftu_apply(dftu_handle h, void* psi_out, dftu_prec prec, int nbands, int64_t ld_band, const double* coef,
+                       dftu_stream stream) {
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c) return DFTU_ERR_INVALID_ARG;
+    if (!c->pot_ready || !c->proj_ready) return fail(c, DFTU_ERR_NOT_READY, "apply: call dftu_project and dftu_acbn0_uj first");
+    if (!psi_out || (prec != DFTU_C128 && prec != DFTU_C64) || !valid_stride_args(c, nbands, ld_band) || nbands > c->proj_nbands)
+        return fail(c, DFTU_ERR_INVALID_ARG, "apply: null psi, bad precision, ld_band < npts or nbands outside [1, projected bands]");
+    Guard g(c->device);
+    int64_t sk, ss, sn;
+    strides(c, nbands, ld_band, sk, ss, sn);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_apply(c->v, psi_out, prec, c->f64_mode, nbands, sk, ss, sn, coef ? coef : c->d_coef_one,
+                                 c->d_color_order, c->color_beg, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "apply");
+    c->last_stream = st;
+    return DFTU_OK;
+}
+
+dftu_status dftu_get_results(dftu_handle h, double* n_out, double* U, double* J, double* EU_atom, double* EU_total,
+                             dftu_stream stream) {
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c) return DFTU_ERR_INVALID_ARG;
+    if ((n_out && !c->occ_ready) || ((U || J || EU_atom || EU_total) && !c->pot_ready))
+        return fail(c, DFTU_ERR_NOT_READY, "get_results: the requested quantities have not been computed");
+    Guard g(c->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(st);
+    const int na = (int)c->atoms.size();
+    if (e == cudaSuccess && n_out) {
+        std::vector<double2> rho(c->mat_total);
+        e = cudaMemcpy(rho.data(), c->v.rho, rho.size() * sizeof(double2), cudaMemcpyDeviceToHost);
+        size_t o = 0;
+        for (int a = 0; a < na && e == cudaSuccess; ++a) {
+            const int M = c->M[a];
+            const int D = (c->spin == DFTU_NONCOLLINEAR) ? 2 * M : M;
+            const int nb = (c->spin == DFTU_NONCOLLINEAR) ? 1 : c->ns;
+            for (int b = 0; b < nb; ++b)
+                for (int x = 0; x < D; ++x)
+                    for (int y = 0; y < D; ++y) {   // paper's n_{xy} = rho_{yx}
+                        double2 r = rho[c->mat_off[a] + (size_t)b * D * D + y * D + x];
+                        n_out[2 * o] = r.x;
+                        n_out[2 * o + 1] = r.y;
+                        ++o;
+                    }
+        }
+    }
+    if (e == cudaSuccess && U) e = cudaMemcpy(U, c->v.U, na * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && J) e = cudaMemcpy(J, c->v.J, na * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && EU_atom) e = cudaMemcpy(EU_atom, c->v.E, na * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && EU_total) e = cudaMemcpy(EU_total, c->v.Etot, sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "get_results");
+    return DFTU_OK;
+}
+
+dftu_status dftu_get_renormalized(dftu_handle h, double* Pbar_out, double* Nbar_out, dftu_stream stream) {
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c) return DFTU_ERR_INVALID_ARG;
+    if (!c->occ_ready) return fail(c, DFTU_ERR_NOT_READY, "get_renormalized: call dftu_occupations first");
+    Guard g(c->device);
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    const int na = (int)c->atoms.size();
+    if (e == cudaSuccess && Pbar_out) {
+        std::vector<double2> pb(c->mat_total);
+        e = cudaMemcpy(pb.data(), c->v.pbar, pb.size() * sizeof(double2), cudaMemcpyDeviceToHost);
+        size_t o = 0;
+        for (int a = 0; a < na && e == cudaSuccess; ++a) {
+            const int M = c->M[a];
+            const int D = (c->spin == DFTU_NONCOLLINEAR) ? 2 * M : M;
+            const int nb = (c->spin == DFTU_NONCOLLINEAR) ? 1 : c->ns;
+            for (int b = 0; b < nb; ++b)
+                for (int x = 0; x < D; ++x)
+                    for (int y = 0; y < D; ++y) {
+                        double2 r = pb[c->mat_off[a] + (size_t)b * D * D + y * D + x];
+                        Pbar_out[2 * o] = r.x;
+                        Pbar_out[2 * o + 1] = r.y;
+                        ++o;
+                    }
+        }
+    }
+    if (e == cudaSuccess && Nbar_out) {
+        const int rows = (c->spin == DFTU_NONCOLLINEAR) ? c->nk : c->nk * c->ns;
+        const int nb = c->proj_nbands;
+        for (int r = 0; r < rows && e == cudaSuccess; ++r)
+            e = cudaMemcpy(Nbar_out + (size_t)r * nb * c->nspecies, c->v.nbar + (size_t)r * c->max_bands * c->nspecies,
+                           (size_t)nb * c->nspecies * sizeof(double), cudaMemcpyDeviceToHost);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "get_renormalized");
+    return DFTU_OK;
+}
+
+dftu_status dftu_get_projections(dftu_handle h, double* p_out, dftu_stream stream) {
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c) return DFTU_ERR_INVALID_ARG;
+    if (!c->proj_ready) return fail(c, DFTU_ERR_NOT_READY, "get_projections: call dftu_project first");
+    if (!p_out) return fail(c, DFTU_ERR_INVALID_ARG, "get_projections: null output");
+    Guard g(c->device);
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    const int rows = c->nk * c->ns, nb = c->proj_nbands;
+    for (int r = 0; r < rows && e == cudaSuccess; ++r)
+        e = cudaMemcpy(p_out + 2 * (size_t)r * nb * c->MT, c->v.p + (size_t)r * c->max_bands * c->MT,
+                       (size_t)nb * c->MT * sizeof(double2), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "get_projections");
+    return DFTU_OK;
+}
+
+int dftu_total_orbitals(dftu_handle h) {
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    return (c && c->atoms_ready) ? c->MT : 0;
+}
+
+int dftu_atom_points(dftu_handle h, int atom) {
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c || !c->atoms_ready || atom < 0 || atom >= (int)c->atoms.size()) return 0;
+    return c->npts[atom];
+}
+
+dftu_status dftu_sync_status(dftu_handle h) {
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c) return DFTU_ERR_INVALID_ARG;
+    Guard g(c->device);
+    cudaError_t e = cudaStreamSynchronize(c->last_stream);
+    int st = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&st, c->v.status, sizeof(int), cudaMemcpyDeviceToHost);
+    int zero = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(c->v.status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "sync_status");
+    if (st & ST_NONFINITE) return fail(c, DFTU_ERR_NONFINITE, "a projection was not finite");
+    if (st & ST_TIMEOUT) return fail(c, DFTU_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (st & ST_ZERO_DENOM) return fail(c, DFTU_ERR_ZERO_DENOM, "an ACBN0 denominator was below 1e-14; U = J = 0 there");
+    return DFTU_OK;
+}
+
+const char* dftu_last_error(dftu_handle h) {
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c) return "null handle";
+    return c->err.c_str();
+}
+
+void dftu_destroy(dftu_handle h) {
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c) return;
+    {
+        Guard g(c->device);
+        for (void* p : c->allocs) cudaFree(p);
+    }
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,140 @@
+// Internal definitions shared by the translation units of libdftu.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "dftu.h"
+
+namespace dftu {
+
+constexpr int TILE = 512;      // sphere points per tile (one CTA stages a tile in shared memory)
+constexpr int TILE_PAD = TILE + 128;   // staged orbital rows incl. zero padding read by chained loops (Q*CH <= 128)
+constexpr int MAXM = 7;        // orbitals per shell, l <= 3
+constexpr int IMG_RANGE = 2;   // lattice images |T| <= 2 cells per axis
+constexpr int NIMG = 125;      // (2*IMG_RANGE+1)^3 image ids
+constexpr int CTA = 256;       // threads per CTA of the streaming kernels
+
+enum StatusBits : int { ST_NONFINITE = 1, ST_ZERO_DENOM = 2, ST_TIMEOUT = 4 };
+
+// A tile: up to TILE consecutive points of one (atom, image) segment in GPU point order.
+struct Tile {
+    int atom;
+    int M;          // orbitals of the atom
+    int seg;        // image segment (row of the phase table)
+    int np;         // points in the tile
+    int64_t p0;     // first point, GPU order
+    int64_t phi0;   // element offset of the first point's orbital values ([point][M] layout)
+    int moff;       // slot of this tile's M partial sums in a row of the per-tile partial buffer
+    int color;      // apply colour: tiles of one colour touch disjoint grid points
+};
+
+// Everything a kernel may need, passed by value.
+struct View {
+    int n0, n1, n2;
+    double h0, h1, h2, o0, o1, o2;
+    int periodic;
+    double dV;
+    int nk;
+    int ns;           // stored spin channels (collinear 2, unpolarised 1) or spinor components (2)
+    int noncollinear;
+    int natoms, nspecies;
+    int MT;           // sum over atoms of M
+    int TM;           // sum over tiles of M
+    int ntiles, nseg;
+    int max_bands;
+
+    const double* kvec;      // [nk][3]
+    const double* wk;        // [nk]
+    const double* atom_pos;  // [natoms][3]
+    const double* atom_rad;  // [natoms]
+    const int* atom_M;
+    const int* atom_species;
+    const int* atom_moff;     // offset of the atom's orbitals in [MT]
+    const int* atom_mat_off;  // offset of the atom's matrices (complex elements) in rho/pbar/V
+    const int* atom_tile_beg; // tiles of atom I are [beg, end) in tile order
+    const int* atom_tile_end;
+    const int* species_coul_off;  // offset of (mm'|m''m''') of each species in coul
+    const int* species_M;
+
+    const Tile* tiles;
+    const int* pt_idx;     // [S] wrapped linear index, GPU order
+    const int* pt_u;       // [S][3] unfolded integer coordinates, GPU order
+    double* phi64;         // [sum S_I M_I]
+    float* phi_hi;
+    float* phi_lo;
+    const int* seg_T;      // [nseg][3] lattice image of each segment, in cells
+    double2* seg_phase;    // [nseg][nk] exp(+i k.T)
+
+    double2* p;            // [nk*ns][max_bands][MT]
+    double2* part;         // [nk*ns][max_bands][TM]
+    double* nbar;          // collinear [nk*ns][max_bands][nspecies]; non-collinear [nk][max_bands][nspecies]
+    double2* rho;          // per atom: collinear [ns][M][M]; non-collinear [2M][2M]   (rho = n^T)
+    double2* pbar;         // same layout, renormalised (Eq. 8), transposed like rho
+    double2* V;            // same layout, U_eff (1/2 - rho)
+    const double* coul;
+    const int* coul_set;   // [nspecies] 1 if set
+    double* U;
+    double* J;
+    double* E;             // [natoms]
+    double* Etot;          // [1]
+    const double* fixU;    // [natoms] NaN = ACBN0
+    const double* fixJ;
+    int* status;
+};
+
+// Host-side context behind dftu_handle.
+struct Ctx {
+    int device = 0;
+    dftu_grid grid{};
+    dftu_spin spin = DFTU_COLLINEAR;
+    int nk = 0, ns = 1, max_bands = 0;
+    dftu_f64_mode f64_mode = DFTU_F64_PAIR;
+    std::vector<double> kvec, wk;
+    bool atoms_ready = false, proj_ready = false, occ_ready = false, pot_ready = false;
+    int proj_nbands = 0;
+    cudaStream_t last_stream = nullptr;
+    std::string err;
+
+    // atoms
+    std::vector<dftu_atom> atoms;
+    std::vector<int> M, moff, mat_off, npts, species_M, coul_off;
+    std::vector<std::vector<int>> canon_to_gpu;   // per atom: canonical point -> GPU-order point
+    std::vector<int64_t> atom_p0, atom_phi0;       // first GPU-order point / phi element of each atom
+    std::vector<Tile> tiles;
+    std::vector<int> color_order;                  // tile indices grouped by colour
+    std::vector<int> color_beg;                    // colour c is color_order[color_beg[c] .. color_beg[c+1])
+    std::vector<std::vector<int>> atom_umin;        // per atom minimum unfolded coordinate
+    int nspecies = 0, MT = 0, TM = 0, mat_total = 0;
+    int64_t S = 0, phi_total = 0;
+
+    View v{};
+    std::vector<void*> allocs;   // every device allocation, freed by dftu_destroy
+    int* d_color_order = nullptr;
+    double* d_coef_one = nullptr;
+};
+
+// ---- launchers implemented in the .cu files (all asynchronous on `st`) -------------------------
+cudaError_t launch_sphere_flags(const View& v, const double* pos, const double* rad, const int* box_lo,
+                                const int* box_dim, const int64_t* box_off, int natoms, int64_t nbox,
+                                signed char* flags, cudaStream_t st);
+cudaError_t launch_seg_phases(const View& v, cudaStream_t st);
+cudaError_t launch_orbitals(const View& v, const double* radial_tab, const int* radial_off,
+                            const int* radial_nr, const double* radial_dr, cudaStream_t st);
+cudaError_t launch_lowdin(const View& v, double* work_S, cudaStream_t st);
+
+cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_f64_mode mode, int nbands,
+                           int64_t sk, int64_t ss, int64_t sn, cudaStream_t st);
+cudaError_t launch_nbar(const View& v, int nbands, cudaStream_t st);
+cudaError_t launch_occupations(const View& v, const double* f, int nbands, cudaStream_t st);
+cudaError_t launch_acbn0(const View& v, cudaStream_t st);
+cudaError_t launch_apply(const View& v, void* psi, dftu_prec prec, dftu_f64_mode mode, int nbands,
+                         int64_t sk, int64_t ss, int64_t sn, const double* coef, const int* color_order,
+                         const std::vector<int>& color_beg, cudaStream_t st);
+
+// Coulomb integrals of one atom's orbitals (blocking); W_out [P][P] with P = M(M+1)/2 pair index.
+int coulomb_atom(const View& v, const Ctx& c, int atom, double* V_dev, std::string& err);
+
+}  // namespace dftu

@@ -1,0 +1,241 @@
+// Occupations (Eq. 4), renormalised occupations (Eqs. 8-9), ACBN0 U and J (Eqs. 10-11, B5-B6),
+// Dudarev energy (Eqs. 3, A5) and the Hubbard potential (Eq. 6).  All FP64, fixed summation order.
+//
+// Storage: rho = n^T, i.e. rho_{ab} = sum w f p_a conj(p_b) (a, b = m, or c*M+m for spinors).
+// The paper's n_{ab} is rho_{ba}; the formulas below read it that way.
+#include "dftu_internal.cuh"
+
+namespace dftu {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) { return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y); }  // a conj(b)
+
+// Eq. (9): Nbar per state = sum over atoms of the state's species-mates and m (and spinor components) of |p|^2.
+__global__ void k_nbar(View v, int nbands) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int rows = v.noncollinear ? v.nk : v.nk * v.ns;
+    if (g >= (int64_t)rows * nbands) return;
+    int row = (int)(g / nbands), band = (int)(g % nbands);
+    for (int sp = 0; sp < v.nspecies; ++sp) {
+        double acc = 0.0;
+        for (int a = 0; a < v.natoms; ++a) {
+            if (v.atom_species[a] != sp) continue;
+            int M = v.atom_M[a], mo = v.atom_moff[a];
+            int ncomp = v.noncollinear ? 2 : 1;
+            for (int c = 0; c < ncomp; ++c) {
+                int ks = v.noncollinear ? row * 2 + c : row;
+                const double2* pr = v.p + ((int64_t)ks * v.max_bands + band) * v.MT + mo;
+                for (int m = 0; m < M; ++m) acc += pr[m].x * pr[m].x + pr[m].y * pr[m].y;
+            }
+        }
+        v.nbar[((int64_t)row * v.max_bands + band) * v.nspecies + sp] = acc;
+    }
+}
+
+// Eqs. (4), (8), (A2), (B3): one CTA per (atom, spin channel) [collinear] or per atom [non-collinear].
+// Thread (pair, slice): pair = matrix element (a,b); slices split the (k, band) sum, reduced in order.
+__global__ void k_occupations(View v, const double* __restrict__ f, int nbands) {
+    const int a = blockIdx.x;
+    const int s = blockIdx.y;
+    const int M = v.atom_M[a], mo = v.atom_moff[a], sp = v.atom_species[a];
+    const int D = v.noncollinear ? 2 * M : M;
+    const int P = D * D;
+    const int SL = max(1, (int)blockDim.x / P);
+    const int pair = threadIdx.x % P, slice = threadIdx.x / P;
+    const int ia = pair / D, ib = pair % D;
+    __shared__ double2 red_r[CTA], red_p[CTA];
+    double2 r = make_double2(0.0, 0.0), pb = make_double2(0.0, 0.0);
+    if (slice < SL) {
+        int total = v.nk * nbands;
+        for (int kb = slice; kb < total; kb += SL) {
+            int k = kb / nbands, band = kb % nbands;
+            double2 pa, pbv;
+            double w, nb;
+            if (v.noncollinear) {
+                int ca = ia / M, ma = ia % M, cb = ib / M, mb = ib % M;
+                pa = v.p[((int64_t)(k * 2 + ca) * v.max_bands + band) * v.MT + mo + ma];
+                pbv = v.p[((int64_t)(k * 2 + cb) * v.max_bands + band) * v.MT + mo + mb];
+                w = v.wk[k] * f[(int64_t)k * nbands + band];
+                nb = v.nbar[((int64_t)k * v.max_bands + band) * v.nspecies + sp];
+            } else {
+                int ks = k * v.ns + s;
+                const double2* pr = v.p + ((int64_t)ks * v.max_bands + band) * v.MT + mo;
+                pa = pr[ia];
+                pbv = pr[ib];
+                w = v.wk[k] * f[((int64_t)k * v.ns + s) * nbands + band];
+                nb = v.nbar[((int64_t)ks * v.max_bands + band) * v.nspecies + sp];
+            }
+            double2 c = cmulc(pa, pbv);
+            r.x += w * c.x; r.y += w * c.y;
+            pb.x += w * nb * c.x; pb.y += w * nb * c.y;
+        }
+    }
+    red_r[threadIdx.x] = r;
+    red_p[threadIdx.x] = pb;
+    __syncthreads();
+    if (slice == 0 && threadIdx.x < P) {
+        for (int q = 1; q < SL; ++q) {
+            double2 x = red_r[q * P + pair], y = red_p[q * P + pair];
+            r.x += x.x; r.y += x.y; pb.x += y.x; pb.y += y.y;
+        }
+        int64_t o = v.atom_mat_off[a] + (int64_t)s * P + pair;
+        v.rho[o] = r;
+        v.pbar[o] = pb;
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double x) {
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    return x;
+}
+
+// Eqs. (10)-(11) [collinear/unpolarised] or (B5)-(B6) [non-collinear], then Eq. (3)/(A5) and Eq. (6).
+// One warp per atom; sums are lane-strided then tree-reduced (fixed order).
+__global__ void k_acbn0(View v) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int a = warp; a < v.natoms; a += nw) {
+        const int M = v.atom_M[a], sp = v.atom_species[a];
+        const int64_t mo = v.atom_mat_off[a];
+        const double* Vc = v.coul + v.species_coul_off[sp];
+        const int M2 = M * M, M4 = M2 * M2;
+        double U, J, num_u = 0.0, num_j = 0.0, den_u = 0.0, den_j = 0.0;
+        const bool fixed = !isnan(v.fixU[a]);
+        if (!v.noncollinear) {
+            const int nchan = v.ns;   // stored channels; alpha = 0,1 maps to channel alpha % nchan
+            // paper's Pbar^alpha_{xy} = stored pbar[alpha][y][x]
+            if (!fixed) {
+                for (int e = lane; e < M4; e += 32) {
+                    int x = e / (M2 * M), y = (e / M2) % M, z = (e / M) % M, w = e % M;
+                    double vxyzw = Vc[((x * M + y) * M + z) * M + w];
+                    double vxwzy = Vc[((x * M + w) * M + z) * M + y];
+                    double2 Pt1 = make_double2(0, 0), Pt2 = make_double2(0, 0);
+                    for (int al = 0; al < 2; ++al) {
+                        int c = al % nchan;
+                        double2 p1 = v.pbar[mo + c * M2 + y * M + x], p2 = v.pbar[mo + c * M2 + w * M + z];
+                        Pt1.x += p1.x; Pt1.y += p1.y; Pt2.x += p2.x; Pt2.y += p2.y;
+                        num_j += (p1.x * p2.x - p1.y * p2.y) * vxwzy;
+                    }
+                    num_u += (Pt1.x * Pt2.x - Pt1.y * Pt2.y) * vxyzw;
+                }
+                num_u = warp_sum(num_u);
+                num_j = warp_sum(num_j);
+                double Nt[2] = {0, 0}, N2[2] = {0, 0};
+                for (int al = 0; al < 2; ++al) {
+                    int c = al % nchan;
+                    for (int m = 0; m < M; ++m) {
+                        double N = v.rho[mo + c * M2 + m * M + m].x;
+                        Nt[al] += N;
+                        N2[al] += N * N;
+                    }
+                }
+                double same = (Nt[0] * Nt[0] - N2[0]) + (Nt[1] * Nt[1] - N2[1]);
+                double opp = Nt[0] * Nt[1] + Nt[1] * Nt[0];
+                den_u = same + opp;
+                den_j = same;
+            }
+        } else {
+            const int D = 2 * M;
+            // paper's n^{st}_{xy} = stored rho[(t*M+y)][(s*M+x)]
+            auto PB = [&](int s, int t, int x, int y) { return v.pbar[mo + (t * M + y) * D + (s * M + x)]; };
+            auto NN = [&](int s, int t, int x) { return v.rho[mo + (t * M + x) * D + (s * M + x)]; };
+            if (!fixed) {
+                for (int e = lane; e < M4; e += 32) {
+                    int x = e / (M2 * M), y = (e / M2) % M, z = (e / M) % M, w = e % M;
+                    double vxyzw = Vc[((x * M + y) * M + z) * M + w];
+                    double vxwzy = Vc[((x * M + w) * M + z) * M + y];
+                    double2 d1 = make_double2(0, 0), d2 = make_double2(0, 0);
+                    for (int s = 0; s < 2; ++s) {
+                        double2 q1 = PB(s, s, x, y), q2 = PB(s, s, z, w);
+                        d1.x += q1.x; d1.y += q1.y; d2.x += q2.x; d2.y += q2.y;
+                        for (int t = 0; t < 2; ++t) {
+                            double2 r1 = PB(s, t, x, y), r2 = PB(t, s, z, w);
+                            num_j += (r1.x * r2.x - r1.y * r2.y) * vxwzy;
+                        }
+                    }
+                    num_u += (d1.x * d2.x - d1.y * d2.y) * vxyzw;
+                }
+                num_u = warp_sum(num_u);
+                num_j = warp_sum(num_j);
+                for (int s = 0; s < 2; ++s) {
+                    int o = 1 - s;
+                    for (int x = 0; x < M; ++x)
+                        for (int y = 0; y < M; ++y) {
+                            double2 ss_x = NN(s, s, x), ss_y = NN(s, s, y), oo_y = NN(o, o, y);
+                            double2 so_x = NN(s, o, x), os_y = NN(o, s, y);
+                            den_u += ss_x.x * oo_y.x - ss_x.y * oo_y.y;
+                            if (x != y) {
+                                double nss = ss_x.x * ss_y.x - ss_x.y * ss_y.y;
+                                den_u += nss;
+                                den_j += nss + (so_x.x * os_y.x - so_x.y * os_y.y);
+                            }
+                        }
+                    for (int x = 0; x < M; ++x) {
+                        double2 so = NN(s, o, x), os = NN(o, s, x);
+                        den_u -= so.x * os.x - so.y * os.y;
+                    }
+                }
+            }
+        }
+        bool zero = false;
+        if (fixed) {
+            U = v.fixU[a];
+            J = v.fixJ[a];
+        } else if (fabs(den_u) < 1e-14 || fabs(den_j) < 1e-14) {
+            U = 0.0; J = 0.0; zero = true;
+        } else {
+            U = num_u / den_u;
+            J = num_j / den_j;
+        }
+        const double Ue = U - J;
+        // Energy (Eq. 3 / A5): U_eff/2 sum_blocks (Tr n - Tr n^2); potential (Eq. 6): U_eff (1/2 - rho)
+        const int D = v.noncollinear ? 2 * M : M;
+        const int nblk = v.noncollinear ? 1 : v.ns;
+        double tr = 0.0;
+        for (int b = 0; b < nblk; ++b) {
+            const double2* R = v.rho + mo + (int64_t)b * D * D;
+            double part = 0.0;
+            for (int e = lane; e < D * D; e += 32) {
+                int x = e / D, y = e % D;
+                double2 rxy = R[x * D + y], ryx = R[y * D + x];
+                part -= rxy.x * ryx.x - rxy.y * ryx.y;
+                if (x == y) part += rxy.x;
+                double2 Vv = make_double2(Ue * ((x == y ? 0.5 : 0.0) - rxy.x), -Ue * rxy.y);
+                v.V[mo + (int64_t)b * D * D + e] = Vv;
+            }
+            tr += warp_sum(part);
+        }
+        if (!v.noncollinear && v.ns == 1) tr *= 2.0;
+        if (lane == 0) {
+            v.U[a] = U;
+            v.J[a] = J;
+            v.E[a] = 0.5 * Ue * tr;
+            if (zero) atomicOr(v.status, ST_ZERO_DENOM);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int a = 0; a < v.natoms; ++a) s += v.E[a];
+        v.Etot[0] = s;
+    }
+}
+
+cudaError_t launch_nbar(const View& v, int nbands, cudaStream_t st) {
+    int rows = v.noncollinear ? v.nk : v.nk * v.ns;
+    int64_t n = (int64_t)rows * nbands;
+    k_nbar<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(v, nbands);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_occupations(const View& v, const double* f, int nbands, cudaStream_t st) {
+    dim3 grid(v.natoms, v.noncollinear ? 1 : v.ns);
+    k_occupations<<<grid, CTA, 0, st>>>(v, f, nbands);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_acbn0(const View& v, cudaStream_t st) {
+    k_acbn0<<<1, 1024, 0, st>>>(v);
+    return cudaGetLastError();
+}
+
+}  // namespace dftu

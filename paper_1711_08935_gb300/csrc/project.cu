@@ -1,0 +1,399 @@
+// Sphere gather + projection p = dV sum_j phi_m(j) exp(+i k.T_j) psi(idx_j)   (inside Eqs. 4 and 6).
+//
+// Work decomposition: one CTA per (tile, band chunk, k*spin).  A tile holds up to TILE points of one
+// (atom, lattice image) segment, so its Bloch phase is a single number applied to the tile sum.  The
+// CTA stages the tile's grid indices and orbital values in shared memory once and streams the
+// bands of its chunk: Q adjacent lanes walk the points of one band (Q*16 or Q*8 contiguous bytes
+// per band row when the points run along x), 32/Q bands per warp.  Partial sums per tile are
+// written in FP64 and summed over the tiles of each atom in a fixed order by k_tile_reduce, so
+// results are deterministic.
+//
+// Arithmetic policies
+//   F64  : complex128 states, FP64 FMAs (the FP64 pipe of this GPU runs at ~1/70 of FP32).
+//   PAIR : complex128 states carried as pairs of FP32 numbers.  Each double is split exactly
+//          (integer ops) into hi + lo floats scaled by 2^-Emax of its chain; products accumulate
+//          into an accumulator offset by a power of two C >= 4*sum|terms| so that the running sum
+//          moves in one binade: t = s - acc is exact and the rounding residual a*b - t is caught
+//          in a second float.  Chains are merged with TwoSum.  Accuracy ~2^-44 of the chain scale.
+//   F32  : complex64 states, FP32 orbitals hi + lo, FP32 chunk sums merged with TwoSum per lane,
+//          FP64 across tiles.
+#include "dftu_internal.cuh"
+
+namespace dftu {
+
+// ------------------------------------------------------------------------------------------------
+// small helpers
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+struct DF2 { float2 h, l; };   // (re, im) pair of double-float numbers
+
+// TwoSum(a.h, b.h) with the low parts added: a <- a + b.
+__device__ __forceinline__ void df_add(DF2& a, const DF2& b) {
+    float2 s = fadd2(a.h, b.h);
+    float2 bb = fadd2(s, make_float2(-a.h.x, -a.h.y));
+    float2 e1 = fadd2(a.h, make_float2(-(s.x - bb.x), -(s.y - bb.y)));
+    float2 e2 = fadd2(b.h, make_float2(-bb.x, -bb.y));
+    float2 e = fadd2(e1, e2);
+    float2 l = fadd2(fadd2(a.l, b.l), e);
+    a.h = s;
+    a.l = l;
+}
+
+__device__ __forceinline__ float shfl_x(float x, int off) { return __shfl_xor_sync(0xffffffffu, x, off); }
+__device__ __forceinline__ double shfl_x(double x, int off) { return __shfl_xor_sync(0xffffffffu, x, off); }
+
+__device__ __forceinline__ float pow2f(int e) {   // 2^e as float for e in [-126, 127], 0 below
+    return e < -126 ? 0.0f : __int_as_float((e + 127) << 23);
+}
+
+__device__ __forceinline__ void write_partial(const View& v, const Tile& t, int ks, int band, int m, double re, double im) {
+    int k = ks / v.ns;
+    double2 ph = v.seg_phase[t.seg * v.nk + k];
+    double2 r = make_double2(v.dV * (ph.x * re - ph.y * im), v.dV * (ph.x * im + ph.y * re));
+    v.part[((int64_t)ks * v.max_bands + band) * v.TM + t.moff + m] = r;
+}
+
+struct ProjArgs {
+    const void* psi;
+    int64_t sk, ss, sn;
+    int nbands;
+};
+
+// ------------------------------------------------------------------------------------------------
+// F64 policy
+// ------------------------------------------------------------------------------------------------
+template <int M, int Q>
+__device__ __forceinline__ void proj_body_f64(const View& v, const Tile& t, int ks, int band, const double2* __restrict__ row,
+                                              const int* s_idx, const double* s_phi) {
+    const int q = threadIdx.x & (Q - 1);
+    double2 acc[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) acc[m] = make_double2(0.0, 0.0);
+    if (row) {
+        int i = q;
+        for (; i + 3 * Q < t.np; i += 4 * Q) {
+            double2 x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = __ldg(row + s_idx[i + u * Q]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const double* ph = s_phi + (i + u * Q) * M;
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    acc[m].x = fma(ph[m], x[u].x, acc[m].x);
+                    acc[m].y = fma(ph[m], x[u].y, acc[m].y);
+                }
+            }
+        }
+        for (; i < t.np; i += Q) {
+            double2 x = __ldg(row + s_idx[i]);
+            const double* ph = s_phi + i * M;
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                acc[m].x = fma(ph[m], x.x, acc[m].x);
+                acc[m].y = fma(ph[m], x.y, acc[m].y);
+            }
+        }
+    }
+#pragma unroll
+    for (int off = Q / 2; off > 0; off >>= 1)
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            acc[m].x += shfl_x(acc[m].x, off);
+            acc[m].y += shfl_x(acc[m].y, off);
+        }
+    if (row && q == 0)
+        for (int m = 0; m < M; ++m) write_partial(v, t, ks, band, m, acc[m].x, acc[m].y);
+}
+
+// ------------------------------------------------------------------------------------------------
+// F32 policy (complex64 states)
+// ------------------------------------------------------------------------------------------------
+template <int M, int Q, int CH>
+__device__ __forceinline__ void proj_body_f32(const View& v, const Tile& t, int ks, int band, const float2* __restrict__ row,
+                                              const int* s_idx, const float4* s_phi) {
+    const int q = threadIdx.x & (Q - 1);
+    DF2 R[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) R[m] = DF2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    if (row) {
+        for (int i0 = q; i0 < t.np; i0 += Q * CH) {
+            float2 x[CH];
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                int i = i0 + c * Q;
+                x[c] = (i < t.np) ? __ldg(row + s_idx[i]) : make_float2(0.f, 0.f);
+            }
+            DF2 ch[M];
+#pragma unroll
+            for (int m = 0; m < M; ++m) ch[m] = DF2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const float4* ph = s_phi + (i0 + c * Q) * M;
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    float4 f = ph[m];   // (hi, hi, lo, lo)
+                    ch[m].h = ffma2(make_float2(f.x, f.y), x[c], ch[m].h);
+                    ch[m].l = ffma2(make_float2(f.z, f.w), x[c], ch[m].l);
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < M; ++m) df_add(R[m], ch[m]);
+        }
+    }
+#pragma unroll
+    for (int off = Q / 2; off > 0; off >>= 1)
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            DF2 o{make_float2(shfl_x(R[m].h.x, off), shfl_x(R[m].h.y, off)),
+                  make_float2(shfl_x(R[m].l.x, off), shfl_x(R[m].l.y, off))};
+            df_add(R[m], o);
+        }
+    if (row && q == 0)
+        for (int m = 0; m < M; ++m)
+            write_partial(v, t, ks, band, m, (double)R[m].h.x + (double)R[m].l.x, (double)R[m].h.y + (double)R[m].l.y);
+}
+
+// ------------------------------------------------------------------------------------------------
+// PAIR policy (complex128 states, FP32-pair arithmetic)
+// ------------------------------------------------------------------------------------------------
+// Split a double with biased exponent field <= Em into float hi + lo of x * 2^(1023-Em).
+// hi = top 24 significant bits, lo = the next 23 (error <= 2^-47 |x|).  Values 2^126 below the
+// chain maximum (and zeros/denormals) are flushed.
+__device__ __forceinline__ void split_scaled(double x, int Em, float& hi, float& lo) {
+    unsigned whi = (unsigned)__double2hiint(x), wlo = (unsigned)__double2loint(x);
+    int E = (whi >> 20) & 0x7FF;
+    unsigned sgn = whi & 0x80000000u;
+    unsigned t = __funnelshift_r(wlo, whi, 29);                         // [E8..E0][m51..m29]
+    unsigned hb = (t - ((unsigned)(Em - 127) << 23)) | sgn;
+    bool okh = (E > 0) && (E + 126 >= Em);
+    unsigned ew = ((whi & 0x7FF00000u) << 3) - ((unsigned)(Em - 104) << 23);
+    unsigned f0 = ew | sgn;
+    unsigned f1 = f0 | ((wlo >> 6) & 0x7FFFFFu);
+    bool okl = (E > 0) && (E + 103 >= Em);
+    hi = okh ? __uint_as_float(hb) : 0.0f;
+    lo = okl ? (__uint_as_float(f1) - __uint_as_float(f0)) : 0.0f;
+}
+
+__device__ __forceinline__ int exp_field(double x) { return (__double2hiint(x) >> 20) & 0x7FF; }
+
+template <int M, int Q, int CH>
+__device__ __forceinline__ void proj_body_pair(const View& v, const Tile& t, int ks, int band, const double2* __restrict__ row,
+                                               const int* s_idx, const float4* s_phi, int pe) {
+    const int q = threadIdx.x & (Q - 1);
+    DF2 R[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) R[m] = DF2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    int Em_run = 0;
+    bool bad = false;
+    // chain offset C = 2^(pe + 1 + log2 CH + 2) >= 4 * CH * max|phi x'|, |x'| < 2, |phi| < 2^pe
+    constexpr int LOG2CH = (CH >= 16) ? 4 : (CH >= 8) ? 3 : (CH >= 4) ? 2 : (CH >= 2) ? 1 : 0;
+    const float Cv = pow2f(min(max(pe + 3 + LOG2CH, -100), 100));
+    const float2 C2 = make_float2(Cv, Cv);
+    const float2 mone = make_float2(-1.f, -1.f);
+    if (row) {
+        for (int i0 = q; i0 < t.np; i0 += Q * CH) {
+            double2 x[CH];
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                int i = i0 + c * Q;
+                x[c] = (i < t.np) ? __ldg(row + s_idx[i]) : make_double2(0.0, 0.0);
+            }
+            int Ec = 0;
+#pragma unroll
+            for (int c = 0; c < CH; ++c) Ec = max(Ec, max(exp_field(x[c].x), exp_field(x[c].y)));
+            if (Ec == 0x7FF) bad = true;
+            if (Ec == 0) continue;
+            if (Ec > Em_run) {
+                if (Em_run != 0) {
+                    float s = pow2f(Em_run - Ec);
+                    float2 s2 = make_float2(s, s);
+#pragma unroll
+                    for (int m = 0; m < M; ++m) {
+                        R[m].h = __fmul2_rn(R[m].h, s2);
+                        R[m].l = __fmul2_rn(R[m].l, s2);
+                    }
+                }
+                Em_run = Ec;
+            }
+            float2 acc[M], lo[M];
+#pragma unroll
+            for (int m = 0; m < M; ++m) { acc[m] = C2; lo[m] = make_float2(0.f, 0.f); }
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                float2 bh, bl;
+                split_scaled(x[c].x, Em_run, bh.x, bl.x);
+                split_scaled(x[c].y, Em_run, bh.y, bl.y);
+                const float4* ph = s_phi + (i0 + c * Q) * M;
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    float4 f = ph[m];                                  // (hi, hi, lo, lo)
+                    float2 ah = make_float2(f.x, f.y), al = make_float2(f.z, f.w);
+                    float2 s = ffma2(ah, bh, acc[m]);                  // acc + a*b, rounded
+                    float2 tneg = ffma2(s, mone, acc[m]);              // acc - s  (exact: same binade)
+                    float2 r = ffma2(ah, bh, tneg);                    // rounding residual a*b - (s - acc)
+                    lo[m] = fadd2(lo[m], r);
+                    lo[m] = ffma2(ah, bl, lo[m]);
+                    lo[m] = ffma2(al, bh, lo[m]);
+                    acc[m] = s;
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                DF2 chn{fadd2(acc[m], make_float2(-Cv, -Cv)), lo[m]};  // exact removal of the offset
+                df_add(R[m], chn);
+            }
+        }
+    }
+    // bring the Q lanes of this band to a common scale, then add in pairs
+    int Em_max = Em_run;
+#pragma unroll
+    for (int off = Q / 2; off > 0; off >>= 1) Em_max = max(Em_max, __shfl_xor_sync(0xffffffffu, Em_max, off));
+    if (Em_run != Em_max) {
+        float s = (Em_run == 0) ? 0.0f : pow2f(Em_run - Em_max);
+        float2 s2 = make_float2(s, s);
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            R[m].h = __fmul2_rn(R[m].h, s2);
+            R[m].l = __fmul2_rn(R[m].l, s2);
+        }
+    }
+#pragma unroll
+    for (int off = Q / 2; off > 0; off >>= 1)
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            DF2 o{make_float2(shfl_x(R[m].h.x, off), shfl_x(R[m].h.y, off)),
+                  make_float2(shfl_x(R[m].l.x, off), shfl_x(R[m].l.y, off))};
+            df_add(R[m], o);
+        }
+    unsigned anybad = __any_sync(0xffffffffu, bad);
+    if (row && q == 0) {
+        double sc = ldexp(1.0, Em_max - 1023);
+        for (int m = 0; m < M; ++m) {
+            double re = ((double)R[m].h.x + (double)R[m].l.x) * sc;
+            double im = ((double)R[m].h.y + (double)R[m].l.y) * sc;
+            if (anybad) { re = __longlong_as_double(0x7FF8000000000000LL); im = re; }
+            write_partial(v, t, ks, band, m, re, im);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// kernels
+// ------------------------------------------------------------------------------------------------
+enum Pol { P_F64 = 0, P_PAIR = 1, P_F32 = 2 };
+
+template <int POL, int Q, int CH>
+__global__ void __launch_bounds__(CTA) k_project(View v, ProjArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    int* s_idx = reinterpret_cast<int*>(smem);
+    const Tile t = v.tiles[blockIdx.x];
+    const int ks = blockIdx.z;
+    const int k = ks / v.ns, s = ks % v.ns;
+    constexpr int BPW = 32 / Q;
+    const int band = blockIdx.y * (CTA / 32) * BPW + (threadIdx.x >> 5) * BPW + ((threadIdx.x & 31) / Q);
+
+    for (int i = threadIdx.x; i < TILE; i += CTA) s_idx[i] = (i < t.np) ? v.pt_idx[t.p0 + i] : 0;
+    __shared__ int s_pe;
+    if (POL == P_F64) {
+        double* s_phi = reinterpret_cast<double*>(smem + TILE * sizeof(int));
+        for (int e = threadIdx.x; e < TILE * t.M; e += CTA)
+            s_phi[e] = (e < t.np * t.M) ? v.phi64[t.phi0 + e] : 0.0;
+    } else {
+        float4* s_phi = reinterpret_cast<float4*>(smem + TILE * sizeof(int));
+        if (threadIdx.x == 0) s_pe = -200;
+        __syncthreads();
+        int pe = -200;
+        for (int e = threadIdx.x; e < TILE_PAD * t.M; e += CTA) {
+            float hi = 0.f, lo = 0.f;
+            if (e < t.np * t.M) { hi = v.phi_hi[t.phi0 + e]; lo = v.phi_lo[t.phi0 + e]; }
+            s_phi[e] = make_float4(hi, hi, lo, lo);
+            if (hi != 0.f) pe = max(pe, ((__float_as_int(hi) >> 23) & 0xFF) - 127 + 1);   // |hi| < 2^pe
+        }
+        if (POL == P_PAIR) atomicMax(&s_pe, pe);
+    }
+    __syncthreads();
+
+    const bool active = band < a.nbands;
+    const int64_t off = (int64_t)k * a.sk + (int64_t)s * a.ss + (int64_t)band * a.sn;
+    if (POL == P_F64) {
+        const double* s_phi = reinterpret_cast<const double*>(smem + TILE * sizeof(int));
+        const double2* row = active ? reinterpret_cast<const double2*>(a.psi) + off : nullptr;
+        switch (t.M) {
+            case 1: proj_body_f64<1, Q>(v, t, ks, band, row, s_idx, s_phi); break;
+            case 3: proj_body_f64<3, Q>(v, t, ks, band, row, s_idx, s_phi); break;
+            case 5: proj_body_f64<5, Q>(v, t, ks, band, row, s_idx, s_phi); break;
+            default: proj_body_f64<7, Q>(v, t, ks, band, row, s_idx, s_phi); break;
+        }
+    } else if (POL == P_PAIR) {
+        const float4* s_phi = reinterpret_cast<const float4*>(smem + TILE * sizeof(int));
+        const double2* row = active ? reinterpret_cast<const double2*>(a.psi) + off : nullptr;
+        const int pe = s_pe;
+        switch (t.M) {
+            case 1: proj_body_pair<1, Q, CH>(v, t, ks, band, row, s_idx, s_phi, pe); break;
+            case 3: proj_body_pair<3, Q, CH>(v, t, ks, band, row, s_idx, s_phi, pe); break;
+            case 5: proj_body_pair<5, Q, CH>(v, t, ks, band, row, s_idx, s_phi, pe); break;
+            default: proj_body_pair<7, Q, CH>(v, t, ks, band, row, s_idx, s_phi, pe); break;
+        }
+    } else {
+        const float4* s_phi = reinterpret_cast<const float4*>(smem + TILE * sizeof(int));
+        const float2* row = active ? reinterpret_cast<const float2*>(a.psi) + off : nullptr;
+        switch (t.M) {
+            case 1: proj_body_f32<1, Q, CH>(v, t, ks, band, row, s_idx, s_phi); break;
+            case 3: proj_body_f32<3, Q, CH>(v, t, ks, band, row, s_idx, s_phi); break;
+            case 5: proj_body_f32<5, Q, CH>(v, t, ks, band, row, s_idx, s_phi); break;
+            default: proj_body_f32<7, Q, CH>(v, t, ks, band, row, s_idx, s_phi); break;
+        }
+    }
+}
+
+// p[ks][band][moff_I + m] = sum over the atom's tiles (fixed order) of the tile partials.
+__global__ void k_tile_reduce(View v, int nbands) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t rows = (int64_t)v.nk * v.ns * nbands;
+    if (g >= rows * v.MT) return;
+    int64_t rowi = g / v.MT;
+    int j = (int)(g % v.MT);
+    int ks = (int)(rowi / nbands), band = (int)(rowi % nbands);
+    int a = 0;
+    while (a + 1 < v.natoms && v.atom_moff[a + 1] <= j) ++a;
+    int m = j - v.atom_moff[a];
+    const double2* prow = v.part + ((int64_t)ks * v.max_bands + band) * v.TM;
+    double re = 0.0, im = 0.0;
+    for (int t = v.atom_tile_beg[a]; t < v.atom_tile_end[a]; ++t) {
+        double2 x = prow[v.tiles[t].moff + m];
+        re += x.x;
+        im += x.y;
+    }
+    if (!isfinite(re) || !isfinite(im)) atomicOr(v.status, ST_NONFINITE);
+    v.p[((int64_t)ks * v.max_bands + band) * v.MT + j] = make_double2(re, im);
+}
+
+template <int POL, int Q, int CH>
+static cudaError_t run_project(const View& v, const ProjArgs& a, cudaStream_t st) {
+    static_assert(Q * CH <= TILE_PAD - TILE, "chained loops read up to Q*CH rows past the tile");
+    size_t smem = TILE * sizeof(int) + (size_t)TILE_PAD * MAXM * (POL == P_F64 ? sizeof(double) : sizeof(float4));
+    cudaError_t e = cudaFuncSetAttribute(k_project<POL, Q, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    constexpr int BPC = (CTA / 32) * (32 / Q);
+    dim3 grid(v.ntiles, (a.nbands + BPC - 1) / BPC, v.nk * v.ns);
+    k_project<POL, Q, CH><<<grid, CTA, smem, st>>>(v, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_f64_mode mode, int nbands,
+                           int64_t sk, int64_t ss, int64_t sn, cudaStream_t st) {
+    ProjArgs a{psi, sk, ss, sn, nbands};
+    cudaError_t e;
+    if (prec == DFTU_C64) e = run_project<P_F32, 16, 8>(v, a, st);
+    else if (mode == DFTU_F64_NATIVE) e = run_project<P_F64, 8, 1>(v, a, st);
+    else e = run_project<P_PAIR, 8, 8>(v, a, st);
+    if (e != cudaSuccess) return e;
+    int64_t n = (int64_t)v.nk * v.ns * nbands * v.MT;
+    k_tile_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(v, nbands);
+    return cudaGetLastError();
+}
+
+}  // namespace dftu

@@ -1,0 +1,284 @@
+"""Thin Python binding of libdftu.so (C ABI in include/dftu.h).
+
+Argument marshalling only: every step of the Hubbard-projector path runs in the library's CUDA
+kernels.  Device arrays are torch tensors (PyTorch supplies memory and streams); host-side inputs
+and outputs are numpy arrays.  The library must have been built (paper_1711_08935_gb300.build_lib);
+importing this module without it raises, there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libdftu.so")
+
+DFTU_OK, DFTU_ERR_INVALID_ARG, DFTU_ERR_NOT_READY, DFTU_ERR_ALLOC, DFTU_ERR_CUDA, DFTU_ERR_NONFINITE, \
+    DFTU_ERR_ZERO_DENOM, DFTU_ERR_TIMEOUT = range(8)
+STATUS_NAMES = ["OK", "INVALID_ARG", "NOT_READY", "ALLOC", "CUDA", "NONFINITE", "ZERO_DENOM", "TIMEOUT"]
+C128, C64 = 0, 1
+COLLINEAR, UNPOLARIZED, NONCOLLINEAR = 0, 1, 2
+F64_PAIR, F64_NATIVE = 0, 1
+HARTREE_EV = 27.211386245988
+
+# Every symbol include/dftu.h declares (checked by the CPU tests).
+EXPORTED = ["dftu_create", "dftu_setup_atoms", "dftu_get_sphere", "dftu_coulomb_integrals", "dftu_set_coulomb",
+            "dftu_set_u", "dftu_set_f64_mode", "dftu_project", "dftu_occupations", "dftu_acbn0_uj", "dftu_apply",
+            "dftu_get_results", "dftu_get_renormalized", "dftu_get_projections", "dftu_total_orbitals",
+            "dftu_atom_points", "dftu_sync_status", "dftu_last_error", "dftu_destroy"]
+
+
+class DftuGrid(C.Structure):
+    _fields_ = [("n", C.c_int * 3), ("h", C.c_double * 3), ("origin", C.c_double * 3), ("periodic", C.c_int)]
+
+
+class DftuAtom(C.Structure):
+    _fields_ = [("pos", C.c_double * 3), ("species", C.c_int), ("l", C.c_int), ("radius", C.c_double)]
+
+
+class DftuRadial(C.Structure):
+    _fields_ = [("nr", C.c_int), ("dr", C.c_double), ("R", C.POINTER(C.c_double))]
+
+
+class DftuError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"dftu {STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+_lib: Optional[C.CDLL] = None
+
+
+def load() -> C.CDLL:
+    """Load libdftu.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1711_08935_gb300.build_lib`")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, d, dp, ip = C.c_void_p, C.c_int, C.c_int64, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_int)
+    sig = {
+        "dftu_create": [C.POINTER(vp), C.POINTER(DftuGrid), i32, dp, dp, i32, i32, i32],
+        "dftu_setup_atoms": [vp, i32, C.POINTER(DftuAtom), i32, C.POINTER(DftuRadial), ip],
+        "dftu_get_sphere": [vp, i32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), dp],
+        "dftu_coulomb_integrals": [vp, i32, dp],
+        "dftu_set_coulomb": [vp, i32, dp],
+        "dftu_set_u": [vp, i32, d, d],
+        "dftu_set_f64_mode": [vp, i32],
+        "dftu_project": [vp, vp, i32, i32, i64, vp],
+        "dftu_occupations": [vp, vp, vp],
+        "dftu_acbn0_uj": [vp, vp],
+        "dftu_apply": [vp, vp, i32, i32, i64, vp, vp],
+        "dftu_get_results": [vp, dp, dp, dp, dp, dp, vp],
+        "dftu_get_renormalized": [vp, dp, dp, vp],
+        "dftu_get_projections": [vp, dp, vp],
+        "dftu_total_orbitals": [vp],
+        "dftu_atom_points": [vp, i32],
+        "dftu_sync_status": [vp],
+        "dftu_last_error": [vp],
+        "dftu_destroy": [vp],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    L.dftu_last_error.restype = C.c_char_p
+    L.dftu_destroy.restype = None
+    _lib = L
+    return L
+
+
+def _dp(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _stream_ptr(stream, device) -> C.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    return C.c_void_p(s.cuda_stream)
+
+
+class Handle:
+    """One DFT+U context on one GPU: geometry, orbitals, work buffers.  Calls map 1:1 to the C ABI."""
+
+    def __init__(self, grid, kpts, wk, spin: int, max_bands: int, device: int = 0):
+        self.lib = load()
+        self.device = device
+        self.spin = spin
+        self.nk = len(kpts)
+        self.ns = 1 if spin == UNPOLARIZED else 2
+        self.max_bands = max_bands
+        self.npts_grid = int(np.prod(grid.n))
+        g = DftuGrid((C.c_int * 3)(*grid.n), (C.c_double * 3)(*grid.h), (C.c_double * 3)(*grid.origin),
+                     1 if grid.periodic else 0)
+        kv = np.ascontiguousarray(np.asarray(kpts, dtype=np.float64).reshape(-1, 3))
+        w = np.ascontiguousarray(np.asarray(wk, dtype=np.float64))
+        h = C.c_void_p()
+        self._check(self.lib.dftu_create(C.byref(h), C.byref(g), self.nk, _dp(kv), _dp(w), spin, max_bands, device), None)
+        self.h = h
+        self.M = []
+        self.species = []
+        self.natoms = 0
+
+    # ------------------------------------------------------------------ plumbing
+    def _check(self, status: int, h=-1):
+        if status != DFTU_OK:
+            hh = self.h if h == -1 else h
+            msg = self.lib.dftu_last_error(hh).decode() if hh else ""
+            raise DftuError(status, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dftu_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ set-up
+    def setup_atoms(self, atoms: Sequence, radials: Sequence) -> np.ndarray:
+        arr = (DftuAtom * len(atoms))()
+        for i, a in enumerate(atoms):
+            arr[i] = DftuAtom((C.c_double * 3)(*a.pos), a.species, a.l, a.radius)
+        self._radial_keep = [np.ascontiguousarray(r.R, dtype=np.float64) for r in radials]
+        rr = (DftuRadial * len(radials))()
+        for i, r in enumerate(radials):
+            rr[i] = DftuRadial(len(self._radial_keep[i]), r.dr, _dp(self._radial_keep[i]))
+        npts = (C.c_int * len(atoms))()
+        self._check(self.lib.dftu_setup_atoms(self.h, len(atoms), arr, len(radials), rr, npts))
+        self.M = [2 * a.l + 1 for a in atoms]
+        self.species = [a.species for a in atoms]
+        self.natoms = len(atoms)
+        return np.array(list(npts))
+
+    def get_sphere(self, atom: int):
+        n = self.lib.dftu_atom_points(self.h, atom)
+        idx = np.zeros(n, dtype=np.int32)
+        img = np.zeros((n, 3), dtype=np.int32)
+        phi = np.zeros((n, self.M[atom]), dtype=np.float64)
+        self._check(self.lib.dftu_get_sphere(self.h, atom, idx.ctypes.data_as(C.POINTER(C.c_int32)),
+                                             img.ctypes.data_as(C.POINTER(C.c_int32)), _dp(phi)))
+        return idx, img, phi
+
+    def coulomb_integrals(self, species: int) -> np.ndarray:
+        M = self.M[self.species.index(species)]
+        V = np.zeros((M, M, M, M))
+        self._check(self.lib.dftu_coulomb_integrals(self.h, species, _dp(V)))
+        return V
+
+    def set_coulomb(self, species: int, V: np.ndarray):
+        self._check(self.lib.dftu_set_coulomb(self.h, species, _dp(np.ascontiguousarray(V, dtype=np.float64))))
+
+    def set_u(self, atom: int, U: float, J: float):
+        self._check(self.lib.dftu_set_u(self.h, atom, float(U), float(J)))
+
+    def set_f64_mode(self, mode: int):
+        self._check(self.lib.dftu_set_f64_mode(self.h, mode))
+
+    # ------------------------------------------------------------------ hot path
+    def _psi_args(self, psi: torch.Tensor):
+        if psi.dtype == torch.complex128:
+            prec = C128
+        elif psi.dtype == torch.complex64:
+            prec = C64
+        else:
+            raise TypeError("psi must be complex128 or complex64")
+        if not psi.is_cuda or not psi.is_contiguous():
+            raise ValueError("psi must be a contiguous CUDA tensor")
+        if self.spin == NONCOLLINEAR:
+            if psi.dim() != 4 or psi.shape[0] != self.nk or psi.shape[2] != 2:
+                raise ValueError("non-collinear psi must be [nk][nbands][2][npts]")
+            nb = psi.shape[1]
+        else:
+            if psi.dim() != 4 or psi.shape[0] != self.nk or psi.shape[1] != self.ns:
+                raise ValueError("psi must be [nk][nspin][nbands][npts]")
+            nb = psi.shape[2]
+        if psi.shape[3] < self.npts_grid:
+            raise ValueError("psi's last dimension is shorter than the grid")
+        return prec, nb, psi.shape[3]
+
+    def project(self, psi: torch.Tensor, stream=None):
+        prec, nb, ld = self._psi_args(psi)
+        self._check(self.lib.dftu_project(self.h, C.c_void_p(psi.data_ptr()), prec, nb, ld, _stream_ptr(stream, self.device)))
+
+    def occupations(self, f: torch.Tensor, stream=None):
+        if f.dtype != torch.float64 or not f.is_cuda or not f.is_contiguous():
+            raise ValueError("f must be a contiguous float64 CUDA tensor")
+        self._check(self.lib.dftu_occupations(self.h, C.c_void_p(f.data_ptr()), _stream_ptr(stream, self.device)))
+
+    def acbn0_uj(self, stream=None):
+        self._check(self.lib.dftu_acbn0_uj(self.h, _stream_ptr(stream, self.device)))
+
+    def apply(self, psi: torch.Tensor, coef: Optional[torch.Tensor] = None, stream=None):
+        prec, nb, ld = self._psi_args(psi)
+        cp = None
+        if coef is not None:
+            if coef.dtype != torch.complex128 or not coef.is_cuda:
+                raise ValueError("coef must be a complex128 CUDA tensor")
+            cp = C.c_void_p(coef.data_ptr())
+        self._check(self.lib.dftu_apply(self.h, C.c_void_p(psi.data_ptr()), prec, nb, ld, cp, _stream_ptr(stream, self.device)))
+
+    # ------------------------------------------------------------------ results
+    def _mat_sizes(self):
+        if self.spin == NONCOLLINEAR:
+            return [(1, 2 * M) for M in self.M]
+        return [(self.ns, M) for M in self.M]
+
+    def _unpack_mats(self, flat: np.ndarray):
+        out, o = [], 0
+        for nb, D in self._mat_sizes():
+            n = nb * D * D
+            out.append((flat[2 * o:2 * (o + n):2] + 1j * flat[2 * o + 1:2 * (o + n):2]).reshape(nb, D, D))
+            o += n
+        return out
+
+    def results(self, stream=None) -> dict:
+        tot = sum(nb * D * D for nb, D in self._mat_sizes())
+        n = np.zeros(2 * tot)
+        U, J, E = np.zeros(self.natoms), np.zeros(self.natoms), np.zeros(self.natoms)
+        Et = np.zeros(1)
+        self._check(self.lib.dftu_get_results(self.h, _dp(n), _dp(U), _dp(J), _dp(E), _dp(Et), _stream_ptr(stream, self.device)))
+        return dict(n=self._unpack_mats(n), U=U, J=J, EU_atom=E, EU=float(Et[0]))
+
+    def occupation_matrices(self, stream=None):
+        tot = sum(nb * D * D for nb, D in self._mat_sizes())
+        n = np.zeros(2 * tot)
+        self._check(self.lib.dftu_get_results(self.h, _dp(n), None, None, None, None, _stream_ptr(stream, self.device)))
+        return self._unpack_mats(n)
+
+    def renormalized(self, nbands: int, stream=None):
+        tot = sum(nb * D * D for nb, D in self._mat_sizes())
+        P = np.zeros(2 * tot)
+        rows = self.nk if self.spin == NONCOLLINEAR else self.nk * self.ns
+        nsp = max(self.species) + 1
+        Nb = np.zeros(rows * nbands * nsp)
+        self._check(self.lib.dftu_get_renormalized(self.h, _dp(P), _dp(Nb), _stream_ptr(stream, self.device)))
+        return self._unpack_mats(P), Nb.reshape(rows, nbands, nsp)
+
+    def projections(self, nbands: int, stream=None) -> np.ndarray:
+        MT = self.lib.dftu_total_orbitals(self.h)
+        rows = self.nk * self.ns if self.spin != NONCOLLINEAR else self.nk * 2
+        p = np.zeros(2 * rows * nbands * MT)
+        self._check(self.lib.dftu_get_projections(self.h, _dp(p), _stream_ptr(stream, self.device)))
+        return (p[0::2] + 1j * p[1::2]).reshape(rows, nbands, MT)
+
+    def sync_status(self) -> int:
+        return self.lib.dftu_sync_status(self.h)
+
+
+def handle_for_system(system, max_bands: int, device: int = 0) -> Handle:
+    """Create a handle for a synthetic System (see synth.py) and set up its atoms."""
+    spin = NONCOLLINEAR if system.noncollinear else (UNPOLARIZED if system.nspin == 1 else COLLINEAR)
+    h = Handle(system.grid, system.kpts, system.wk, spin, max_bands, device)
+    h.setup_atoms(system.atoms, system.radials)
+    return h
