@@ -117,6 +117,16 @@ dftu_status dftu_set_u(dftu_handle h, int atom, double U, double J);
 /* Choose the arithmetic for DFTU_C128 states (see dftu_f64_mode). */
 dftu_status dftu_set_f64_mode(dftu_handle h, dftu_f64_mode mode);
 
+/* Kernel variant for one of the streaming kernels (the library's autotuner in the Python binding picks
+ * them by timing): which = 0 projection of complex128 states, 1 projection of complex64 states,
+ * 2 apply of complex128 states, 3 apply of complex64 states; variant indexes a fixed table of
+ * (lanes per band, points per chain, band groups per CTA) shapes, 0 = default.  Results do not depend
+ * on the variant beyond floating-point summation order. */
+dftu_status dftu_set_kernel_variant(dftu_handle h, int which, int variant);
+
+/* Number of kernel variants available for `which` (see dftu_set_kernel_variant); 0 for a bad `which`. */
+int dftu_kernel_variants(int which);
+
 /* Projections p^{k,s}_{I,m,n} = dV sum_j phi_{I,m}(j) exp(+i k.T_j) psi_{k,s,n}(idx_j) of the first
  * nbands bands (nbands <= max_bands) of psi (device, layout above) onto every atom's orbitals.
  * DFTU_C64 states are multiplied by FP32 orbitals with an FP32 low-part correction, summed in FP32

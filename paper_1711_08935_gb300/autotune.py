@@ -1,0 +1,43 @@
+"""Autotuner for the streaming kernels: times every shape variant of the projection and apply
+kernels (dftu_set_kernel_variant) on the caller's own states with CUDA events and keeps the fastest.
+The apply variants modify the states in place, as the apply always does."""
+from __future__ import annotations
+
+import torch
+
+from . import dftu
+
+WHICH = {("project", torch.complex128): 0, ("project", torch.complex64): 1,
+         ("apply", torch.complex128): 2, ("apply", torch.complex64): 3}
+
+
+def _time(fn, reps, stream):
+    fn()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def autotune(h: dftu.Handle, psi: torch.Tensor, reps: int = 3) -> dict:
+    """Pick the fastest projection and apply variants for psi's precision; returns the timings (ms).
+    The handle must already hold a potential (dftu_acbn0_uj) for the apply to run."""
+    stream = torch.cuda.current_stream(psi.device)
+    out = {}
+    for kind in ("project", "apply"):
+        which = WHICH[(kind, psi.dtype)]
+        n = h.lib.dftu_kernel_variants(which)
+        times = []
+        for v in range(n):
+            h.set_kernel_variant(which, v)
+            fn = (lambda: h.project(psi)) if kind == "project" else (lambda: h.apply(psi))
+            times.append(_time(fn, reps, stream))
+        best = min(range(n), key=lambda i: times[i])
+        h.set_kernel_variant(which, best)
+        out[kind] = {"variant": best, "ms": [round(t, 4) for t in times]}
+    h.project(psi)      # leave fresh projections of the current states in the handle
+    return out

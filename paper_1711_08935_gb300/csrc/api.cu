@@ -371,6 +371,7 @@ dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, 
     if (e == cudaSuccess) e = upload(c, &c->d_color_order, c->color_order);
     if (e != cudaSuccess) return cuda_fail(c, e, "setup_atoms: upload");
     v.natoms = natoms; v.nspecies = nspecies; v.MT = MT; v.TM = TM; v.ntiles = (int)c->tiles.size(); v.nseg = nseg;
+    v.maxM = *std::max_element(c->M.begin(), c->M.end());
     v.atom_pos = d_pos; v.atom_rad = d_rad; v.atom_M = d_aM; v.atom_species = d_asp; v.atom_moff = d_amoff;
     v.atom_mat_off = d_amat; v.atom_tile_beg = d_tb; v.atom_tile_end = d_te; v.species_coul_off = d_coff; v.species_M = d_spM;
     v.tiles = dt; v.pt_idx = d_idx; v.pt_u = d_u; v.seg_T = d_segT; v.seg_phase = d_segph;
@@ -495,6 +496,17 @@ dftu_status dftu_set_f64_mode(dftu_handle h, dftu_f64_mode mode) {
     return DFTU_OK;
 }
 
+dftu_status dftu_set_kernel_variant(dftu_handle h, int which, int variant) {
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c) return DFTU_ERR_INVALID_ARG;
+    if (which < 0 || which > 3 || variant < 0 || variant >= NVARIANTS)
+        return fail(c, DFTU_ERR_INVALID_ARG, "set_kernel_variant: which must be 0..3 and variant 0.." + std::to_string(NVARIANTS - 1));
+    c->variant[which] = variant;
+    return DFTU_OK;
+}
+
+int dftu_kernel_variants(int which) { return (which >= 0 && which <= 3) ? NVARIANTS : 0; }
+
 dftu_status dftu_project(dftu_handle h, const void* psi, dftu_prec prec, int nbands, int64_t ld_band, dftu_stream stream) {
     Ctx* c = reinterpret_cast<Ctx*>(h);
     if (!c) return DFTU_ERR_INVALID_ARG;
@@ -505,7 +517,7 @@ dftu_status dftu_project(dftu_handle h, const void* psi, dftu_prec prec, int nba
     int64_t sk, ss, sn;
     strides(c, nbands, ld_band, sk, ss, sn);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    cudaError_t e = launch_project(c->v, psi, prec, c->f64_mode, nbands, sk, ss, sn, st);
+    cudaError_t e = launch_project(c->v, psi, prec, c->f64_mode, nbands, sk, ss, sn, c->variant[prec == DFTU_C64 ? 1 : 0], st);
     if (e != cudaSuccess) return cuda_fail(c, e, "project");
     c->last_stream = st;
     c->proj_ready = true;
@@ -562,7 +574,7 @@ dftu_status dftu_apply(dftu_handle h, void* psi_out, dftu_prec prec, int nbands,
     strides(c, nbands, ld_band, sk, ss, sn);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = launch_apply(c->v, psi_out, prec, c->f64_mode, nbands, sk, ss, sn, coef ? coef : c->d_coef_one,
-                                 c->d_color_order, c->color_beg, st);
+                                 c->d_color_order, c->color_beg, c->variant[prec == DFTU_C64 ? 3 : 2], st);
     if (e != cudaSuccess) return cuda_fail(c, e, "apply");
     c->last_stream = st;
     return DFTU_OK;

@@ -36,9 +36,51 @@ __device__ __forceinline__ double f2d_bits(float f) {
     return e == 0 ? 0.0 : __hiloint2double((int)hi, (int)lo);
 }
 
-template <int POL, int Q, int M>
+__device__ __forceinline__ float pow2f(int e) { return e < -126 ? 0.0f : __int_as_float((e + 127) << 23); }
+
+__device__ __forceinline__ int exp_field_d(double x) { return (__double2hiint(x) >> 20) & 0x7FF; }
+
+// Split a double with exponent field <= Em into floats hi + lo of x * 2^(1023-Em) (47 significant bits;
+// zeros, denormals and values 2^126 below 2^(Em-1023) flush to zero).  Integer operations only.
+__device__ __forceinline__ void split_scaled_d(double x, int Em, float& hi, float& lo) {
+    unsigned whi = (unsigned)__double2hiint(x), wlo = (unsigned)__double2loint(x);
+    int E = (whi >> 20) & 0x7FF;
+    unsigned sgn = whi & 0x80000000u;
+    unsigned t = __funnelshift_r(wlo, whi, 29);
+    unsigned hb = (t - ((unsigned)(Em - 127) << 23)) | sgn;
+    unsigned ew = ((whi & 0x7FF00000u) << 3) - ((unsigned)(Em - 104) << 23);
+    unsigned f0 = ew | sgn;
+    unsigned f1 = f0 | ((wlo >> 6) & 0x7FFFFFu);
+    hi = (E > 0 && E + 126 >= Em) ? __uint_as_float(hb) : 0.0f;
+    lo = (E > 0 && E + 103 >= Em) ? (__uint_as_float(f1) - __uint_as_float(f0)) : 0.0f;
+}
+
+// Nearest double to (h + l) * 2^sc for a normalised float pair (|l| <= ulp(h)/2), assembled with
+// integer operations: the bit pattern of h as a double plus l counted in units of that double's ulp
+// (half-ulps when h is a power of two and l points toward zero).
+__device__ __forceinline__ double pair_to_double(float h, float l, int sc) {
+    unsigned u = __float_as_uint(h);
+    int e = (u >> 23) & 0xFF;
+    if (e == 0) return 0.0;
+    unsigned hi = (u & 0x80000000u) | ((unsigned)(e + 896 + sc) << 20) | ((u & 0x7FFFFFu) >> 3);
+    unsigned lo = u << 29;
+    unsigned lu = __float_as_uint(l);
+    int el = (lu >> 23) & 0xFF;
+    // t = l * 2^(179 - e): exponent-field add (|t| <= 2^28, no overflow); sign flipped to magnitude direction
+    unsigned tb = (lu + ((unsigned)(179 - e) << 23)) ^ (u & 0x80000000u);
+    float tm = (el == 0) ? 0.0f : __uint_as_float(tb);
+    if ((u & 0x7FFFFFu) == 0 && tm < 0.0f) tm *= 2.0f;
+    long long K = (long long)__float2int_rn(tm);
+    unsigned long long D = (((unsigned long long)hi << 32) | lo) + (unsigned long long)K;
+    return __longlong_as_double((long long)D);
+}
+
+// Each lane handles U points of its band at a time: U loads in flight, then the arithmetic, then U
+// stores (the points of one tile are distinct grid points, so the batch never aliases).  Orbital rows
+// up to Q*U past the tile are staged as zeros, so the arithmetic needs no bounds test.
+template <int POL, int Q, int M, int U>
 __device__ __forceinline__ void apply_body(const Tile& t, const ApplyArgs& a, int64_t off, int q, int bl, const int* s_idx,
-                                           const unsigned char* after_idx, const unsigned char* after_c) {
+                                           const unsigned char* after_idx, const unsigned char* after_c, int pe) {
     if (POL == A_F64) {
         double2* row = reinterpret_cast<double2*>(a.psi) + off;
         const double* s_phi = reinterpret_cast<const double*>(after_c);
@@ -46,22 +88,34 @@ __device__ __forceinline__ void apply_body(const Tile& t, const ApplyArgs& a, in
         double2 cc[M];
 #pragma unroll
         for (int m = 0; m < M; ++m) cc[m] = s_c[bl * MAXM + m];
-        for (int i = q; i < t.np; i += Q) {
-            int idx = s_idx[i];
-            double2 x = row[idx];
-            const double* ph = s_phi + i * M;
+        for (int i0 = q; i0 < t.np; i0 += Q * U) {
+            double2 x[U];
 #pragma unroll
-            for (int m = 0; m < M; ++m) {
-                x.x = fma(ph[m], cc[m].x, x.x);
-                x.y = fma(ph[m], cc[m].y, x.y);
+            for (int u = 0; u < U; ++u) {
+                int i = i0 + u * Q;
+                x[u] = (i < t.np) ? row[s_idx[i]] : make_double2(0.0, 0.0);
             }
-            row[idx] = x;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const double* ph = s_phi + (i0 + u * Q) * M;
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    x[u].x = fma(ph[m], cc[m].x, x[u].x);
+                    x[u].y = fma(ph[m], cc[m].y, x[u].y);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                int i = i0 + u * Q;
+                if (i < t.np) row[s_idx[i]] = x[u];
+            }
         }
     } else if (POL == A_PAIR) {
-        // delta = sum_m phi_m c_m as a float pair (TwoProd of the leading products, TwoSum of the
-        // running sum, FP32 corrections), then psi + delta with two FP64 additions per component.
+        // delta = sum_m phi_m c_m with the offset accumulator (C >= 4 sum|phi c|, residuals caught in a
+        // second float), then psi + delta as FP32 pairs at a common scale 2^(Em-1023), and the rounded
+        // double assembled with integer operations: no FP64 instruction on this path.
         double2* row = reinterpret_cast<double2*>(a.psi) + off;
-        const float2* s_phi = reinterpret_cast<const float2*>(after_c);
+        const float4* s_phi = reinterpret_cast<const float4*>(after_c);
         const float4* s_c = reinterpret_cast<const float4*>(after_idx);
         float2 ch[M], cl[M];
 #pragma unroll
@@ -70,146 +124,205 @@ __device__ __forceinline__ void apply_body(const Tile& t, const ApplyArgs& a, in
             ch[m] = make_float2(c4.x, c4.y);
             cl[m] = make_float2(c4.z, c4.w);
         }
-        for (int i = q; i < t.np; i += Q) {
-            int idx = s_idx[i];
-            double2 x = row[idx];
-            const float2* ph = s_phi + i * M;
-            float2 sh = make_float2(0.f, 0.f), sl = make_float2(0.f, 0.f);
+        int ce = -126;                                               // |c_hi| < 2^ce
 #pragma unroll
-            for (int m = 0; m < M; ++m) {
-                float2 f = ph[m];
-                float2 fh = make_float2(f.x, f.x), fl = make_float2(f.y, f.y);
-                float2 pr = __fmul2_rn(fh, ch[m]);
-                float2 pe = __ffma2_rn(fh, ch[m], make_float2(-pr.x, -pr.y));   // exact product error
-                float2 s2 = __fadd2_rn(sh, pr);                                   // TwoSum(sh, pr)
-                float2 bb = __fadd2_rn(s2, make_float2(-sh.x, -sh.y));
-                float2 e = __fadd2_rn(__fadd2_rn(sh, make_float2(-(s2.x - bb.x), -(s2.y - bb.y))),
-                                      __fadd2_rn(pr, make_float2(-bb.x, -bb.y)));
-                sh = s2;
-                sl = __fadd2_rn(sl, __fadd2_rn(e, pe));
-                sl = __ffma2_rn(fh, cl[m], sl);
-                sl = __ffma2_rn(fl, ch[m], sl);
+        for (int m = 0; m < M; ++m)
+            ce = max(ce, max((__float_as_int(ch[m].x) >> 23) & 0xFF, (__float_as_int(ch[m].y) >> 23) & 0xFF) - 126);
+        const int ebound = min(max(pe + ce, -120), 120);          // |phi_hi c_hi| < 2^ebound
+        const float Cv = pow2f(ebound + 5);
+        const float2 C2 = make_float2(Cv, Cv), mone = make_float2(-1.f, -1.f);
+        const int Ed = ebound + 3 + 1023;                           // |delta| < 2^(Ed-1023)
+        for (int i0 = q; i0 < t.np; i0 += Q * U) {
+            double2 x[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                int i = i0 + u * Q;
+                x[u] = (i < t.np) ? row[s_idx[i]] : make_double2(0.0, 0.0);
             }
-            x.x = (x.x + f2d_bits(sh.x)) + f2d_bits(sl.x);
-            x.y = (x.y + f2d_bits(sh.y)) + f2d_bits(sl.y);
-            row[idx] = x;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const float4* ph = s_phi + (i0 + u * Q) * M;
+                float2 acc = C2, lo = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    float4 f = ph[m];                                      // (hi, hi, lo, lo)
+                    float2 fh = make_float2(f.x, f.y), fl = make_float2(f.z, f.w);
+                    float2 sacc = __ffma2_rn(fh, ch[m], acc);
+                    float2 tneg = __ffma2_rn(sacc, mone, acc);             // acc - sacc, exact
+                    float2 r = __ffma2_rn(fh, ch[m], tneg);
+                    lo = __fadd2_rn(lo, r);
+                    lo = __ffma2_rn(fh, cl[m], lo);
+                    lo = __ffma2_rn(fl, ch[m], lo);
+                    acc = sacc;
+                }
+                float2 dh = __fadd2_rn(acc, make_float2(-Cv, -Cv));          // exact
+                int Em = max(max(exp_field_d(x[u].x), exp_field_d(x[u].y)), Ed);
+                float2 xh, xl;
+                split_scaled_d(x[u].x, Em, xh.x, xl.x);
+                split_scaled_d(x[u].y, Em, xh.y, xl.y);
+                int k = 1023 - Em, k1 = k / 2;
+                float2 s1 = make_float2(pow2f(k1), pow2f(k1)), s2 = make_float2(pow2f(k - k1), pow2f(k - k1));
+                dh = __fmul2_rn(__fmul2_rn(dh, s1), s2);
+                float2 dl = __fmul2_rn(__fmul2_rn(lo, s1), s2);
+                // TwoSum(xh, dh), then the low parts, then renormalise (Fast2Sum)
+                float2 sum = __fadd2_rn(xh, dh);
+                float2 bb = __fadd2_rn(sum, make_float2(-xh.x, -xh.y));
+                float2 e = __fadd2_rn(__fadd2_rn(xh, make_float2(-(sum.x - bb.x), -(sum.y - bb.y))),
+                                      __fadd2_rn(dh, make_float2(-bb.x, -bb.y)));
+                e = __fadd2_rn(e, __fadd2_rn(xl, dl));
+                float2 hh = __fadd2_rn(sum, e);
+                float2 ll = __fadd2_rn(e, make_float2(-(hh.x - sum.x), -(hh.y - sum.y)));
+                x[u].x = pair_to_double(hh.x, ll.x, Em - 1023);
+                x[u].y = pair_to_double(hh.y, ll.y, Em - 1023);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                int i = i0 + u * Q;
+                if (i < t.np) row[s_idx[i]] = x[u];
+            }
         }
     } else {
         float2* row = reinterpret_cast<float2*>(a.psi) + off;
-        const float2* s_phi = reinterpret_cast<const float2*>(after_c);
+        const float4* s_phi = reinterpret_cast<const float4*>(after_c);
         const float2* s_c = reinterpret_cast<const float2*>(after_idx);
         float2 cc[M];
 #pragma unroll
         for (int m = 0; m < M; ++m) cc[m] = s_c[bl * MAXM + m];
-        for (int i = q; i < t.np; i += Q) {
-            int idx = s_idx[i];
-            float2 x = row[idx];
-            const float2* ph = s_phi + i * M;
+        for (int i0 = q; i0 < t.np; i0 += Q * U) {
+            float2 x[U];
 #pragma unroll
-            for (int m = 0; m < M; ++m) x = __ffma2_rn(make_float2(ph[m].x, ph[m].x), cc[m], x);
-            row[idx] = x;
+            for (int u = 0; u < U; ++u) {
+                int i = i0 + u * Q;
+                x[u] = (i < t.np) ? row[s_idx[i]] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const float4* ph = s_phi + (i0 + u * Q) * M;
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    float4 f = ph[m];
+                    x[u] = __ffma2_rn(make_float2(f.x, f.y), cc[m], x[u]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                int i = i0 + u * Q;
+                if (i < t.np) row[s_idx[i]] = x[u];
+            }
         }
     }
 }
 
-template <int POL, int Q>
-__global__ void __launch_bounds__(CTA) k_apply(View v, ApplyArgs a) {
+template <int POL, int Q, int NBG, int U>
+__global__ void __launch_bounds__(CTA, 3) k_apply(View v, ApplyArgs a) {
+    static_assert(Q * U <= TILE_PAD - TILE, "batched loops read up to Q*U rows past the tile");
     extern __shared__ __align__(16) unsigned char smem[];
     int* s_idx = reinterpret_cast<int*>(smem);
     constexpr int BPW = 32 / Q;
     constexpr int BPC = (CTA / 32) * BPW;
+    __shared__ int s_pe;
     const Tile t = v.tiles[a.tile_list[blockIdx.x]];
     const int ks = blockIdx.z;
     const int k = ks / v.ns, s = ks % v.ns;
-    const int band0 = blockIdx.y * BPC;
     const int M = t.M;
     unsigned char* after_idx = smem + TILE * sizeof(int);
-    // coefficient table [BPC][M] complex: FP64 (F64), (hi.re,hi.im,lo.re,lo.im) (PAIR), float2 (F32)
-    double2* s_c64 = reinterpret_cast<double2*>(after_idx);
-    float4* s_c4 = reinterpret_cast<float4*>(after_idx);
-    float2* s_c32 = reinterpret_cast<float2*>(after_idx);
-    unsigned char* after_c = after_idx + BPC * MAXM * sizeof(double2);
+    // coefficient table [BPC][MAXM] in 16-byte slots: double2 (F64), (hi.re, hi.im, lo.re, lo.im) (PAIR), float2 (F32)
+    unsigned char* after_c = after_idx + BPC * MAXM * 16;
 
+    // ---- stage the tile once: grid indices and orbital rows (+ the orbitals' exponent bound)
+    if (threadIdx.x == 0) s_pe = -200;
     for (int i = threadIdx.x; i < TILE; i += CTA) s_idx[i] = (i < t.np) ? v.pt_idx[t.p0 + i] : 0;
-    if (threadIdx.x < BPC * M) {
-        int bl = threadIdx.x / M, m = threadIdx.x % M;
-        int band = band0 + bl;
-        double2 c = make_double2(0.0, 0.0);
-        if (band < a.nbands) {
-            const int mo = v.atom_moff[t.atom];
-            const int64_t vo = v.atom_mat_off[t.atom];
-            double re = 0.0, im = 0.0;
-            if (!v.noncollinear) {
-                const double2* Vm = v.V + vo + (int64_t)s * M * M + m * M;
-                const double2* pr = v.p + ((int64_t)ks * v.max_bands + band) * v.MT + mo;
-                for (int q = 0; q < M; ++q) {
-                    double2 A = Vm[q], B = pr[q];
-                    re += A.x * B.x - A.y * B.y;
-                    im += A.x * B.y + A.y * B.x;
-                }
-            } else {
-                const int D = 2 * M;
-                const double2* Vm = v.V + vo + (int64_t)(s * M + m) * D;
-                for (int c2 = 0; c2 < 2; ++c2) {
-                    const double2* pr = v.p + ((int64_t)(k * 2 + c2) * v.max_bands + band) * v.MT + mo;
-                    for (int q = 0; q < M; ++q) {
-                        double2 A = Vm[c2 * M + q], B = pr[q];
-                        re += A.x * B.x - A.y * B.y;
-                        im += A.x * B.y + A.y * B.x;
-                    }
-                }
-            }
-            double2 ph = v.seg_phase[t.seg * v.nk + k];   // exp(+ikT); the scatter uses its conjugate
-            double2 cf = *reinterpret_cast<const double2*>(a.coef);
-            double2 pc = make_double2(cf.x * ph.x + cf.y * ph.y, cf.y * ph.x - cf.x * ph.y);   // cf * conj(ph)
-            c = make_double2(pc.x * re - pc.y * im, pc.x * im + pc.y * re);
-        }
-        if (POL == A_F64) s_c64[bl * MAXM + m] = c;
-        else if (POL == A_PAIR) {
-            float hr, lr, hi, li;
-            dsplit(c.x, hr, lr);
-            dsplit(c.y, hi, li);
-            s_c4[bl * MAXM + m] = make_float4(hr, hi, lr, li);
-        } else s_c32[bl * MAXM + m] = make_float2((float)c.x, (float)c.y);
-    }
+    __syncthreads();
     if (POL == A_F64) {
         double* s_phi = reinterpret_cast<double*>(after_c);
-        for (int e = threadIdx.x; e < TILE * M; e += CTA) s_phi[e] = (e < t.np * M) ? v.phi64[t.phi0 + e] : 0.0;
+        for (int e = threadIdx.x; e < TILE_PAD * M; e += CTA) s_phi[e] = (e < t.np * M) ? v.phi64[t.phi0 + e] : 0.0;
     } else {
-        float2* s_phi = reinterpret_cast<float2*>(after_c);
-        for (int e = threadIdx.x; e < TILE * M; e += CTA)
-            s_phi[e] = (e < t.np * M) ? make_float2(v.phi_hi[t.phi0 + e], v.phi_lo[t.phi0 + e]) : make_float2(0.f, 0.f);
+        float4* s_phi = reinterpret_cast<float4*>(after_c);
+        int pe = -200;
+        for (int e = threadIdx.x; e < TILE_PAD * M; e += CTA) {
+            float hi = 0.f, lo = 0.f;
+            if (e < t.np * M) { hi = v.phi_hi[t.phi0 + e]; lo = v.phi_lo[t.phi0 + e]; }
+            s_phi[e] = make_float4(hi, hi, lo, lo);
+            if (hi != 0.f) pe = max(pe, ((__float_as_int(hi) >> 23) & 0xFF) - 126);
+        }
+        if (POL == A_PAIR) atomicMax(&s_pe, pe);
     }
-    __syncthreads();
-
     const int lane = threadIdx.x & 31;
     const int bl = (threadIdx.x >> 5) * BPW + lane / Q;
     const int q = lane & (Q - 1);
-    const int band = band0 + bl;
-    if (band >= a.nbands) return;
-    const int64_t off = (int64_t)k * a.sk + (int64_t)s * a.ss + (int64_t)band * a.sn;
-    switch (M) {
-        case 1: apply_body<POL, Q, 1>(t, a, off, q, bl, s_idx, after_idx, after_c); break;
-        case 3: apply_body<POL, Q, 3>(t, a, off, q, bl, s_idx, after_idx, after_c); break;
-        case 5: apply_body<POL, Q, 5>(t, a, off, q, bl, s_idx, after_idx, after_c); break;
-        default: apply_body<POL, Q, 7>(t, a, off, q, bl, s_idx, after_idx, after_c); break;
+    const int mo = v.atom_moff[t.atom];
+    const int64_t vo = v.atom_mat_off[t.atom];
+    for (int g = 0; g < NBG; ++g) {
+        const int band0 = (blockIdx.y * NBG + g) * BPC;
+        if (band0 >= a.nbands) break;
+        __syncthreads();   // staging done / previous group's readers done with the coefficient table
+        if (threadIdx.x < BPC * M) {
+            int cb = threadIdx.x / M, m = threadIdx.x % M;
+            int band = band0 + cb;
+            double2 c = make_double2(0.0, 0.0);
+            if (band < a.nbands) {
+                double re = 0.0, im = 0.0;
+                if (!v.noncollinear) {
+                    const double2* Vm = v.V + vo + (int64_t)s * M * M + m * M;
+                    const double2* pr = v.p + ((int64_t)ks * v.max_bands + band) * v.MT + mo;
+                    for (int qq = 0; qq < M; ++qq) {
+                        double2 A = Vm[qq], B = pr[qq];
+                        re += A.x * B.x - A.y * B.y;
+                        im += A.x * B.y + A.y * B.x;
+                    }
+                } else {
+                    const int D = 2 * M;
+                    const double2* Vm = v.V + vo + (int64_t)(s * M + m) * D;
+                    for (int c2 = 0; c2 < 2; ++c2) {
+                        const double2* pr = v.p + ((int64_t)(k * 2 + c2) * v.max_bands + band) * v.MT + mo;
+                        for (int qq = 0; qq < M; ++qq) {
+                            double2 A = Vm[c2 * M + qq], B = pr[qq];
+                            re += A.x * B.x - A.y * B.y;
+                            im += A.x * B.y + A.y * B.x;
+                        }
+                    }
+                }
+                double2 ph = v.seg_phase[t.seg * v.nk + k];   // exp(+ikT); the scatter uses its conjugate
+                double2 cf = *reinterpret_cast<const double2*>(a.coef);
+                double2 pc = make_double2(cf.x * ph.x + cf.y * ph.y, cf.y * ph.x - cf.x * ph.y);   // cf * conj(ph)
+                c = make_double2(pc.x * re - pc.y * im, pc.x * im + pc.y * re);
+            }
+            if (POL == A_F64) reinterpret_cast<double2*>(after_idx)[cb * MAXM + m] = c;
+            else if (POL == A_PAIR) {
+                float hr, lr, hi, li;
+                dsplit(c.x, hr, lr);
+                dsplit(c.y, hi, li);
+                reinterpret_cast<float4*>(after_idx)[cb * MAXM + m] = make_float4(hr, hi, lr, li);
+            } else reinterpret_cast<float2*>(after_idx)[cb * MAXM + m] = make_float2((float)c.x, (float)c.y);
+        }
+        __syncthreads();
+        const int band = band0 + bl;
+        if (band < a.nbands) {
+            const int64_t off = (int64_t)k * a.sk + (int64_t)s * a.ss + (int64_t)band * a.sn;
+            const int pe = s_pe;
+            switch (M) {
+                case 1: apply_body<POL, Q, 1, U>(t, a, off, q, bl, s_idx, after_idx, after_c, pe); break;
+                case 3: apply_body<POL, Q, 3, U>(t, a, off, q, bl, s_idx, after_idx, after_c, pe); break;
+                case 5: apply_body<POL, Q, 5, U>(t, a, off, q, bl, s_idx, after_idx, after_c, pe); break;
+                default: apply_body<POL, Q, 7, U>(t, a, off, q, bl, s_idx, after_idx, after_c, pe); break;
+            }
+        }
     }
 }
 
-template <int POL, int Q>
+template <int POL, int Q, int NBG, int U>
 static cudaError_t run_apply(const View& v, ApplyArgs a, const int* color_order, const std::vector<int>& color_beg,
                              cudaStream_t st) {
     constexpr int BPC = (CTA / 32) * (32 / Q);
-    size_t smem = TILE * sizeof(int) + BPC * MAXM * sizeof(double2) +
-                  (size_t)TILE * MAXM * (POL == A_F64 ? sizeof(double) : sizeof(float2));
-    cudaError_t e = cudaFuncSetAttribute(k_apply<POL, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    size_t smem = TILE * sizeof(int) + BPC * MAXM * 16 + (size_t)TILE_PAD * v.maxM * (POL == A_F64 ? sizeof(double) : sizeof(float4));
+    cudaError_t e = cudaFuncSetAttribute(k_apply<POL, Q, NBG, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     for (size_t c = 0; c + 1 < color_beg.size(); ++c) {
         int n = color_beg[c + 1] - color_beg[c];
         if (n == 0) continue;
         a.tile_list = color_order + color_beg[c];
-        dim3 grid(n, (a.nbands + BPC - 1) / BPC, v.nk * v.ns);
-        k_apply<POL, Q><<<grid, CTA, smem, st>>>(v, a);
+        dim3 grid(n, (a.nbands + BPC * NBG - 1) / (BPC * NBG), v.nk * v.ns);
+        k_apply<POL, Q, NBG, U><<<grid, CTA, smem, st>>>(v, a);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -218,11 +331,23 @@ static cudaError_t run_apply(const View& v, ApplyArgs a, const int* color_order,
 
 cudaError_t launch_apply(const View& v, void* psi, dftu_prec prec, dftu_f64_mode mode, int nbands,
                          int64_t sk, int64_t ss, int64_t sn, const double* coef, const int* color_order,
-                         const std::vector<int>& color_beg, cudaStream_t st) {
+                         const std::vector<int>& color_beg, int variant, cudaStream_t st) {
     ApplyArgs a{psi, sk, ss, sn, nbands, coef, nullptr};
-    if (prec == DFTU_C64) return run_apply<A_F32, 16>(v, a, color_order, color_beg, st);
-    if (mode == DFTU_F64_NATIVE) return run_apply<A_F64, 8>(v, a, color_order, color_beg, st);
-    return run_apply<A_PAIR, 8>(v, a, color_order, color_beg, st);
+    if (prec == DFTU_C64) {
+        switch (variant) {   // (lanes per band, band groups per CTA, points in flight per lane)
+            case 1: return run_apply<A_F32, 8, 4, 4>(v, a, color_order, color_beg, st);
+            case 2: return run_apply<A_F32, 4, 4, 8>(v, a, color_order, color_beg, st);
+            case 3: return run_apply<A_F32, 16, 4, 4>(v, a, color_order, color_beg, st);
+            default: return run_apply<A_F32, 8, 4, 8>(v, a, color_order, color_beg, st);
+        }
+    }
+    if (mode == DFTU_F64_NATIVE) return run_apply<A_F64, 8, 4, 4>(v, a, color_order, color_beg, st);
+    switch (variant) {
+        case 1: return run_apply<A_PAIR, 8, 4, 2>(v, a, color_order, color_beg, st);
+        case 2: return run_apply<A_PAIR, 4, 4, 4>(v, a, color_order, color_beg, st);
+        case 3: return run_apply<A_PAIR, 8, 4, 8>(v, a, color_order, color_beg, st);
+        default: return run_apply<A_PAIR, 8, 4, 4>(v, a, color_order, color_beg, st);
+    }
 }
 
 }  // namespace dftu

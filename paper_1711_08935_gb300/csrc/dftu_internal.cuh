@@ -45,6 +45,7 @@ struct View {
     int TM;           // sum over tiles of M
     int ntiles, nseg;
     int max_bands;
+    int maxM;         // largest shell present (sizes the staged orbital rows)
 
     const double* kvec;      // [nk][3]
     const double* wk;        // [nk]
@@ -95,6 +96,7 @@ struct Ctx {
     std::vector<double> kvec, wk;
     bool atoms_ready = false, proj_ready = false, occ_ready = false, pot_ready = false;
     int proj_nbands = 0;
+    int variant[4] = {0, 0, 0, 0};   // project c128, project c64, apply c128, apply c64
     cudaStream_t last_stream = nullptr;
     std::string err;
 
@@ -125,14 +127,15 @@ cudaError_t launch_orbitals(const View& v, const double* radial_tab, const int* 
                             const int* radial_nr, const double* radial_dr, cudaStream_t st);
 cudaError_t launch_lowdin(const View& v, double* work_S, cudaStream_t st);
 
+constexpr int NVARIANTS = 4;   // shapes per streaming kernel (see dftu_set_kernel_variant)
 cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_f64_mode mode, int nbands,
-                           int64_t sk, int64_t ss, int64_t sn, cudaStream_t st);
+                           int64_t sk, int64_t ss, int64_t sn, int variant, cudaStream_t st);
 cudaError_t launch_nbar(const View& v, int nbands, cudaStream_t st);
 cudaError_t launch_occupations(const View& v, const double* f, int nbands, cudaStream_t st);
 cudaError_t launch_acbn0(const View& v, cudaStream_t st);
 cudaError_t launch_apply(const View& v, void* psi, dftu_prec prec, dftu_f64_mode mode, int nbands,
                          int64_t sk, int64_t ss, int64_t sn, const double* coef, const int* color_order,
-                         const std::vector<int>& color_beg, cudaStream_t st);
+                         const std::vector<int>& color_beg, int variant, cudaStream_t st);
 
 // Coulomb integrals of one atom's orbitals (blocking); W_out [P][P] with P = M(M+1)/2 pair index.
 int coulomb_atom(const View& v, const Ctx& c, int atom, double* V_dev, std::string& err);

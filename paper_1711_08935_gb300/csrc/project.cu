@@ -285,26 +285,27 @@ __device__ __forceinline__ void proj_body_pair(const View& v, const Tile& t, int
 // ------------------------------------------------------------------------------------------------
 enum Pol { P_F64 = 0, P_PAIR = 1, P_F32 = 2 };
 
-template <int POL, int Q, int CH>
-__global__ void __launch_bounds__(CTA) k_project(View v, ProjArgs a) {
+template <int POL, int Q, int CH, int NBG>
+__global__ void __launch_bounds__(CTA, 2) k_project(View v, ProjArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     int* s_idx = reinterpret_cast<int*>(smem);
     const Tile t = v.tiles[blockIdx.x];
     const int ks = blockIdx.z;
     const int k = ks / v.ns, s = ks % v.ns;
     constexpr int BPW = 32 / Q;
-    const int band = blockIdx.y * (CTA / 32) * BPW + (threadIdx.x >> 5) * BPW + ((threadIdx.x & 31) / Q);
+    constexpr int BPC = (CTA / 32) * BPW;
 
-    for (int i = threadIdx.x; i < TILE; i += CTA) s_idx[i] = (i < t.np) ? v.pt_idx[t.p0 + i] : 0;
+    // ---- stage the tile once (grid indices, orbital rows, orbital exponent bound)
     __shared__ int s_pe;
+    if (threadIdx.x == 0) s_pe = -200;
+    for (int i = threadIdx.x; i < TILE; i += CTA) s_idx[i] = (i < t.np) ? v.pt_idx[t.p0 + i] : 0;
+    __syncthreads();
     if (POL == P_F64) {
         double* s_phi = reinterpret_cast<double*>(smem + TILE * sizeof(int));
         for (int e = threadIdx.x; e < TILE * t.M; e += CTA)
             s_phi[e] = (e < t.np * t.M) ? v.phi64[t.phi0 + e] : 0.0;
     } else {
         float4* s_phi = reinterpret_cast<float4*>(smem + TILE * sizeof(int));
-        if (threadIdx.x == 0) s_pe = -200;
-        __syncthreads();
         int pe = -200;
         for (int e = threadIdx.x; e < TILE_PAD * t.M; e += CTA) {
             float hi = 0.f, lo = 0.f;
@@ -316,35 +317,41 @@ __global__ void __launch_bounds__(CTA) k_project(View v, ProjArgs a) {
     }
     __syncthreads();
 
-    const bool active = band < a.nbands;
-    const int64_t off = (int64_t)k * a.sk + (int64_t)s * a.ss + (int64_t)band * a.sn;
-    if (POL == P_F64) {
-        const double* s_phi = reinterpret_cast<const double*>(smem + TILE * sizeof(int));
-        const double2* row = active ? reinterpret_cast<const double2*>(a.psi) + off : nullptr;
-        switch (t.M) {
-            case 1: proj_body_f64<1, Q>(v, t, ks, band, row, s_idx, s_phi); break;
-            case 3: proj_body_f64<3, Q>(v, t, ks, band, row, s_idx, s_phi); break;
-            case 5: proj_body_f64<5, Q>(v, t, ks, band, row, s_idx, s_phi); break;
-            default: proj_body_f64<7, Q>(v, t, ks, band, row, s_idx, s_phi); break;
-        }
-    } else if (POL == P_PAIR) {
-        const float4* s_phi = reinterpret_cast<const float4*>(smem + TILE * sizeof(int));
-        const double2* row = active ? reinterpret_cast<const double2*>(a.psi) + off : nullptr;
-        const int pe = s_pe;
-        switch (t.M) {
-            case 1: proj_body_pair<1, Q, CH>(v, t, ks, band, row, s_idx, s_phi, pe); break;
-            case 3: proj_body_pair<3, Q, CH>(v, t, ks, band, row, s_idx, s_phi, pe); break;
-            case 5: proj_body_pair<5, Q, CH>(v, t, ks, band, row, s_idx, s_phi, pe); break;
-            default: proj_body_pair<7, Q, CH>(v, t, ks, band, row, s_idx, s_phi, pe); break;
-        }
-    } else {
-        const float4* s_phi = reinterpret_cast<const float4*>(smem + TILE * sizeof(int));
-        const float2* row = active ? reinterpret_cast<const float2*>(a.psi) + off : nullptr;
-        switch (t.M) {
-            case 1: proj_body_f32<1, Q, CH>(v, t, ks, band, row, s_idx, s_phi); break;
-            case 3: proj_body_f32<3, Q, CH>(v, t, ks, band, row, s_idx, s_phi); break;
-            case 5: proj_body_f32<5, Q, CH>(v, t, ks, band, row, s_idx, s_phi); break;
-            default: proj_body_f32<7, Q, CH>(v, t, ks, band, row, s_idx, s_phi); break;
+    // ---- stream NBG groups of BPC bands over the staged tile
+    for (int g = 0; g < NBG; ++g) {
+        const int band0 = (blockIdx.y * NBG + g) * BPC;
+        if (band0 >= a.nbands) break;
+        const int band = band0 + (threadIdx.x >> 5) * BPW + ((threadIdx.x & 31) / Q);
+        const bool active = band < a.nbands;
+        const int64_t off = (int64_t)k * a.sk + (int64_t)s * a.ss + (int64_t)band * a.sn;
+        if (POL == P_F64) {
+            const double* s_phi = reinterpret_cast<const double*>(smem + TILE * sizeof(int));
+            const double2* row = active ? reinterpret_cast<const double2*>(a.psi) + off : nullptr;
+            switch (t.M) {
+                case 1: proj_body_f64<1, Q>(v, t, ks, band, row, s_idx, s_phi); break;
+                case 3: proj_body_f64<3, Q>(v, t, ks, band, row, s_idx, s_phi); break;
+                case 5: proj_body_f64<5, Q>(v, t, ks, band, row, s_idx, s_phi); break;
+                default: proj_body_f64<7, Q>(v, t, ks, band, row, s_idx, s_phi); break;
+            }
+        } else if (POL == P_PAIR) {
+            const float4* s_phi = reinterpret_cast<const float4*>(smem + TILE * sizeof(int));
+            const double2* row = active ? reinterpret_cast<const double2*>(a.psi) + off : nullptr;
+            const int pe = s_pe;
+            switch (t.M) {
+                case 1: proj_body_pair<1, Q, CH>(v, t, ks, band, row, s_idx, s_phi, pe); break;
+                case 3: proj_body_pair<3, Q, CH>(v, t, ks, band, row, s_idx, s_phi, pe); break;
+                case 5: proj_body_pair<5, Q, CH>(v, t, ks, band, row, s_idx, s_phi, pe); break;
+                default: proj_body_pair<7, Q, CH>(v, t, ks, band, row, s_idx, s_phi, pe); break;
+            }
+        } else {
+            const float4* s_phi = reinterpret_cast<const float4*>(smem + TILE * sizeof(int));
+            const float2* row = active ? reinterpret_cast<const float2*>(a.psi) + off : nullptr;
+            switch (t.M) {
+                case 1: proj_body_f32<1, Q, CH>(v, t, ks, band, row, s_idx, s_phi); break;
+                case 3: proj_body_f32<3, Q, CH>(v, t, ks, band, row, s_idx, s_phi); break;
+                case 5: proj_body_f32<5, Q, CH>(v, t, ks, band, row, s_idx, s_phi); break;
+                default: proj_body_f32<7, Q, CH>(v, t, ks, band, row, s_idx, s_phi); break;
+            }
         }
     }
 }
@@ -371,25 +378,39 @@ __global__ void k_tile_reduce(View v, int nbands) {
     v.p[((int64_t)ks * v.max_bands + band) * v.MT + j] = make_double2(re, im);
 }
 
-template <int POL, int Q, int CH>
+template <int POL, int Q, int CH, int NBG>
 static cudaError_t run_project(const View& v, const ProjArgs& a, cudaStream_t st) {
     static_assert(Q * CH <= TILE_PAD - TILE, "chained loops read up to Q*CH rows past the tile");
-    size_t smem = TILE * sizeof(int) + (size_t)TILE_PAD * MAXM * (POL == P_F64 ? sizeof(double) : sizeof(float4));
-    cudaError_t e = cudaFuncSetAttribute(k_project<POL, Q, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    size_t smem = TILE * sizeof(int) + (size_t)TILE_PAD * v.maxM * (POL == P_F64 ? sizeof(double) : sizeof(float4));
+    cudaError_t e = cudaFuncSetAttribute(k_project<POL, Q, CH, NBG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     constexpr int BPC = (CTA / 32) * (32 / Q);
-    dim3 grid(v.ntiles, (a.nbands + BPC - 1) / BPC, v.nk * v.ns);
-    k_project<POL, Q, CH><<<grid, CTA, smem, st>>>(v, a);
+    dim3 grid(v.ntiles, (a.nbands + BPC * NBG - 1) / (BPC * NBG), v.nk * v.ns);
+    k_project<POL, Q, CH, NBG><<<grid, CTA, smem, st>>>(v, a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_f64_mode mode, int nbands,
-                           int64_t sk, int64_t ss, int64_t sn, cudaStream_t st) {
+                           int64_t sk, int64_t ss, int64_t sn, int variant, cudaStream_t st) {
     ProjArgs a{psi, sk, ss, sn, nbands};
     cudaError_t e;
-    if (prec == DFTU_C64) e = run_project<P_F32, 16, 8>(v, a, st);
-    else if (mode == DFTU_F64_NATIVE) e = run_project<P_F64, 8, 1>(v, a, st);
-    else e = run_project<P_PAIR, 8, 8>(v, a, st);
+    if (prec == DFTU_C64) {
+        switch (variant) {   // (lanes per band, points per chain, band groups per CTA)
+            case 1: e = run_project<P_F32, 8, 8, 4>(v, a, st); break;
+            case 2: e = run_project<P_F32, 16, 8, 4>(v, a, st); break;
+            case 3: e = run_project<P_F32, 4, 16, 4>(v, a, st); break;
+            default: e = run_project<P_F32, 8, 16, 4>(v, a, st); break;
+        }
+    } else if (mode == DFTU_F64_NATIVE) {
+        e = run_project<P_F64, 8, 1, 4>(v, a, st);
+    } else {
+        switch (variant) {
+            case 1: e = run_project<P_PAIR, 8, 4, 4>(v, a, st); break;
+            case 2: e = run_project<P_PAIR, 4, 8, 4>(v, a, st); break;
+            case 3: e = run_project<P_PAIR, 8, 8, 1>(v, a, st); break;
+            default: e = run_project<P_PAIR, 8, 8, 4>(v, a, st); break;
+        }
+    }
     if (e != cudaSuccess) return e;
     int64_t n = (int64_t)v.nk * v.ns * nbands * v.MT;
     k_tile_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(v, nbands);

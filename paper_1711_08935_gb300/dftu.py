@@ -29,7 +29,8 @@ HARTREE_EV = 27.211386245988
 EXPORTED = ["dftu_create", "dftu_setup_atoms", "dftu_get_sphere", "dftu_coulomb_integrals", "dftu_set_coulomb",
             "dftu_set_u", "dftu_set_f64_mode", "dftu_project", "dftu_occupations", "dftu_acbn0_uj", "dftu_apply",
             "dftu_get_results", "dftu_get_renormalized", "dftu_get_projections", "dftu_total_orbitals",
-            "dftu_atom_points", "dftu_sync_status", "dftu_last_error", "dftu_destroy"]
+            "dftu_atom_points", "dftu_sync_status", "dftu_last_error", "dftu_destroy",
+            "dftu_set_kernel_variant", "dftu_kernel_variants"]
 
 
 class DftuGrid(C.Structure):
@@ -82,6 +83,8 @@ def load() -> C.CDLL:
         "dftu_sync_status": [vp],
         "dftu_last_error": [vp],
         "dftu_destroy": [vp],
+        "dftu_set_kernel_variant": [vp, i32, i32],
+        "dftu_kernel_variants": [i32],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -184,6 +187,9 @@ class Handle:
 
     def set_f64_mode(self, mode: int):
         self._check(self.lib.dftu_set_f64_mode(self.h, mode))
+
+    def set_kernel_variant(self, which: int, variant: int):
+        self._check(self.lib.dftu_set_kernel_variant(self.h, which, variant))
 
     # ------------------------------------------------------------------ hot path
     def _psi_args(self, psi: torch.Tensor):

@@ -14,7 +14,7 @@ are hydrogen-like stand-ins for the pseudo-atomic orbitals of Sec. II.
 States are built from atom-centred Gaussian-type functions (a functional form
 the method never uses), Bloch-summed over neighbouring images with the phase
 exp(i k.T), mixed with seeded random coefficients, given full-grid noise and
-orthonormalised with a QR factorisation under the grid inner product.
+orthonormalised (Cholesky QR, twice) under the grid inner product.
 """
 from __future__ import annotations
 
@@ -221,6 +221,17 @@ def _gaussian_basis(system: System, k: np.ndarray, alpha: Sequence[float], devic
     return out.to(dtype) if dtype != torch.complex128 else out
 
 
+def _orthonormalise_rows(A: torch.Tensor, dV: float) -> torch.Tensor:
+    """Rows of A made orthonormal under <a|b> = dV sum conj(a) b by Cholesky QR applied twice; the
+    small Gram matrices are factorised on the host (numpy), the products run where A lives."""
+    for _ in range(2):
+        Gm = (A @ A.conj().transpose(0, 1)) * dV
+        L = np.linalg.cholesky(Gm.cpu().numpy())
+        Linv = np.linalg.inv(L)
+        A = torch.from_numpy(Linv).to(A.device) @ A
+    return A
+
+
 def make_states(system: System, nbands: int, seed: int, device="cpu", noise: float = 0.05,
                 spin_bias: Optional[Sequence[float]] = None, dtype=torch.complex128) -> torch.Tensor:
     """Orthonormal (grid inner product with dV) states.
@@ -258,8 +269,7 @@ def make_states(system: System, nbands: int, seed: int, device="cpu", noise: flo
                 psi = psi + noise * scale * nz
                 cols.append(psi)
             A = torch.cat(cols, dim=1) if ncomp == 2 else cols[0]   # [nbands, ncomp*npts]
-            Q, _ = torch.linalg.qr(A.transpose(0, 1))               # [ncomp*npts, nbands]
-            Q = Q.transpose(0, 1) / math.sqrt(g.dV)
+            Q = _orthonormalise_rows(A, g.dV)
             if system.noncollinear:
                 out[ik] = Q.reshape(nbands, 2, g.npts)
             else:
