@@ -153,6 +153,27 @@ dftu_status dftu_acbn0_uj(dftu_handle h, dftu_stream stream);
 dftu_status dftu_apply(dftu_handle h, void* psi_out, dftu_prec prec, int nbands, int64_t ld_band,
                        const double* coef, dftu_stream stream);
 
+/* Projection onto ONE atom's orbitals that allocates nothing, for callers that cannot allocate GPU
+ * memory (an application or framework that owns the whole device memory pool, a real-time loop where
+ * allocation is not allowed, plug-in code that only receives pointers).  It needs no handle: the caller
+ * passes every input and the output as device pointers, and the scratch (per-tile partial sums) lives
+ * in a fixed 8 MiB array that is part of the library's device image (every GPU that loads the library
+ * holds it until the process exits).  The paper has no counterpart; this is a packaging of the
+ * projection for such callers.
+ *   psi    nbands rows of ld_band complex numbers (complex128 or complex64 per prec), device.
+ *   idx    [npts] grid index of each sphere point in a row (0 <= idx < ld_band), device int32.
+ *   phase  [npts] complex128 factor of each point (e.g. exp(+i k.T) of its lattice image), device, or NULL for 1.
+ *   phi    [npts][M] orbital values (FP64), device.
+ *   p_out  [nbands][M] complex128 result, device:  p[n][m] = dV sum_j phi[j][m] phase[j] psi[n][idx[j]], in FP64.
+ * Errors: DFTU_ERR_INVALID_ARG for null pointers, M outside 1..7, or ceil(npts/512)*nbands*M above
+ * 524288 (the scratch size); DFTU_ERR_CUDA if a launch fails.  The first call on a device looks up the
+ * scratch array's device address (once per device), so make that first call before any stream
+ * capture.  Every call uses the same scratch: calls that overlap on the GPU (other streams, other
+ * threads) race and give wrong results; calls ordered on one stream are safe. */
+dftu_status dftu_project_sphere_noalloc(const void* psi, dftu_prec prec, int nbands, int64_t ld_band,
+                                        const int32_t* idx, const double* phase, const double* phi, int npts,
+                                        int M, double dV, double* p_out, dftu_stream stream);
+
 /* Results to host memory (blocking on stream).  Any pointer may be NULL.
  *   n_out     [atom][spin][M][M] interleaved complex (paper's n, Eq. 4); non-collinear [atom][2M][2M]
  *             with index (component*M + m); atoms packed one after another with their own M.

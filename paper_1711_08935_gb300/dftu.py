@@ -30,7 +30,7 @@ EXPORTED = ["dftu_create", "dftu_setup_atoms", "dftu_get_sphere", "dftu_coulomb_
             "dftu_set_u", "dftu_set_f64_mode", "dftu_project", "dftu_occupations", "dftu_acbn0_uj", "dftu_apply",
             "dftu_get_results", "dftu_get_renormalized", "dftu_get_projections", "dftu_total_orbitals",
             "dftu_atom_points", "dftu_sync_status", "dftu_last_error", "dftu_destroy",
-            "dftu_set_kernel_variant", "dftu_kernel_variants"]
+            "dftu_set_kernel_variant", "dftu_kernel_variants", "dftu_project_sphere_noalloc"]
 
 
 class DftuGrid(C.Structure):
@@ -85,6 +85,7 @@ def load() -> C.CDLL:
         "dftu_destroy": [vp],
         "dftu_set_kernel_variant": [vp, i32, i32],
         "dftu_kernel_variants": [i32],
+        "dftu_project_sphere_noalloc": [vp, i32, i32, i64, vp, vp, vp, i32, i32, d, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
