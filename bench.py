@@ -31,6 +31,12 @@ METRIC = "DFT+U projector GB/s & %HBM peak; FP32-state vs FP64 speedup at |dn|<=
 UNIT = "GB/s"
 WORKLOAD = "oxide supercell 96^3 h=0.25, 8 TM(3d,R4.5)+8 O(2p,R3.5), 256 bands, 8 k, collinear, FP64 states"
 
+# DRAM bytes per state (one band of one k-point and spin) measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum) on the 64-band oxide case for the kernel variants named here; see
+# profiles/pair_project_apply_oxide_small.md.  Valid only while that variant is the one timed.
+NCU_TRAFFIC_PER_STATE = {("apply", 0): (805.044224e6 + 570.685440e6) / 128,
+                         ("project", 2): (807.277568e6 + 9.275136e6) / 128}
+
 
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -179,7 +185,11 @@ def run_ours(args):
         return total / steps, statistics.mean(proj), statistics.mean(small), statistics.mean(app)
 
     tuned = {}
-    if not args.no_tune:
+    if args.variants:
+        for which, var in enumerate(int(x) for x in args.variants.split(",")):
+            h.set_kernel_variant(which, var)
+        tuned["fixed"] = args.variants
+    elif not args.no_tune:
         from paper_1711_08935_gb300.autotune import autotune
         tuned["c128"] = autotune(h, psi)
         tuned["c64"] = autotune(h, psi32)
@@ -207,6 +217,9 @@ def run_ours(args):
     dom_ms = app64 if dom == "apply" else proj64
     dom_bytes = ab64 if dom == "apply" else pb64
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    chosen = {"project": h.variants_now()[0], "apply": h.variants_now()[2]}
+    tkey = (dom, chosen[dom])
+    traffic = NCU_TRAFFIC_PER_STATE[tkey] * nb * s.nk * 2 if tkey in NCU_TRAFFIC_PER_STATE else None
 
     # ---- end to end through the public API with host (pinned) states
     e2e = None
@@ -223,7 +236,8 @@ def run_ours(args):
                    "l2": "inputs (58 GB of states) far larger than L2; no flush needed",
                    "sphere_points": int(sum(npts)), "bands": nb, "kpoints": s.nk, "spins": 2},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "peak_source": peak_src, "traffic": None,
+                     "frac": round(achieved / peak, 4), "peak_source": peak_src,
+                     "traffic": round(traffic) if traffic else None,
                      "bytes_per_launch": dom_bytes},
         "kernels_ms": {"project": round(proj64, 4), "occupations+acbn0": round(small64, 4), "apply": round(app64, 4),
                        "project_GBps": round(pb64 / (proj64 * 1e-3) / 1e9, 1),
@@ -365,6 +379,7 @@ def main():
     ap.add_argument("--nbands", type=int, default=256)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--variants", default="", help="fixed kernel variants 'p128,p64,a128,a64' instead of tuning")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

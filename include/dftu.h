@@ -149,9 +149,21 @@ dftu_status dftu_acbn0_uj(dftu_handle h, dftu_stream stream);
 /* psi_out(idx_j) += c exp(-i k.T_j) sum_m phi_m(j) (V p)_m for every atom and sphere point (Eq. 6),
  * with p from the last dftu_project (which may have read a different array) and V from the last
  * dftu_acbn0_uj.  coef: device pointer to one complex FP64 number c, or NULL for c = 1.
- * Points shared by several spheres receive every contribution, in a fixed order. */
+ * accumulate = 0 writes psi_out = c V_U psi_projected on the sphere points instead (other grid points
+ * are not touched), so a term vector needs no clearing.  Points shared by several spheres receive
+ * every contribution, in a fixed order. */
 dftu_status dftu_apply(dftu_handle h, void* psi_out, dftu_prec prec, int nbands, int64_t ld_band,
-                       const double* coef, dftu_stream stream);
+                       const double* coef, int accumulate, dftu_stream stream);
+
+/* One real-time step with the adiabatic Hubbard potential (Sec. V, Eq. 15): occupations, U and J and
+ * V_U are rebuilt from the incoming psi (f: device occupations as for dftu_occupations) and held fixed,
+ * then psi <- sum_{j=0}^{order} (-i dt V_U)^j / j! psi, one term at a time: term_j = (-i dt/j) V_U term_{j-1}
+ * is written to `work` (same layout as psi; only its sphere points are used) and added to psi.
+ * order <= 8.  Only the Hubbard term of the Hamiltonian is propagated (the paper does not name its
+ * propagator; 4th-order Taylor with dt = 0.01 a.u. is the workload's choice).  Launches only, no host
+ * synchronisation and no allocation: a CUDA graph can capture it. */
+dftu_status dftu_taylor_step(dftu_handle h, void* psi, void* work, dftu_prec prec, int nbands, int64_t ld_band,
+                             const double* f, double dt, int order, dftu_stream stream);
 
 /* Projection onto ONE atom's orbitals that allocates nothing, for callers that cannot allocate GPU
  * memory (an application or framework that owns the whole device memory pool, a real-time loop where

@@ -111,6 +111,7 @@ dftu_status dftu_create(dftu_handle* out, const dftu_grid* grid, int nk, const d
     if (e == cudaSuccess) e = dalloc(c, &st, 1);
     if (e == cudaSuccess) e = cudaMemset(st, 0, sizeof(int));
     if (e == cudaSuccess) e = upload(c, &one, std::vector<double>{1.0, 0.0});
+    if (e == cudaSuccess) e = dalloc(c, &c->d_taylor, 2 * MAX_TAYLOR);
     if (e != cudaSuccess) {
         for (void* p : c->allocs) cudaFree(p);
         delete c;
@@ -317,6 +318,19 @@ dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, 
         }
         c->color_beg[ncol] = (int)c->color_order.size();
     }
+    // ---- first-cover flags: in colour order, the first tile that reaches a grid point owns it ----
+    std::vector<unsigned char> pt_first(pt_idx.size(), 0);
+    {
+        std::vector<unsigned char> written((size_t)(n0 * n1 * n2), 0);
+        for (int ti : c->color_order) {
+            const Tile& t = c->tiles[ti];
+            for (int i = 0; i < t.np; ++i) {
+                int idx = pt_idx[t.p0 + i];
+                pt_first[t.p0 + i] = written[idx] ? 0 : 1;
+                written[idx] = 1;
+            }
+        }
+    }
     // ---- per-atom tile ranges, species data, radial tables ----
     std::vector<int> tbeg(natoms, 0), tend(natoms, 0);
     for (size_t t = 0; t < c->tiles.size(); ++t) {
@@ -348,6 +362,8 @@ dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, 
     e = upload(c, &dt, c->tiles);
     if (e == cudaSuccess) e = upload(c, &d_idx, pt_idx);
     if (e == cudaSuccess) e = upload(c, &d_u, pt_u);
+    unsigned char* d_first = nullptr;
+    if (e == cudaSuccess) e = upload(c, &d_first, pt_first);
     if (e == cudaSuccess) e = upload(c, &d_segT, seg_T);
     if (e == cudaSuccess) e = dalloc(c, &d_segph, (size_t)nseg * c->nk);
     if (e == cudaSuccess) e = upload(c, &d_aM, aM);
@@ -374,7 +390,9 @@ dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, 
     v.maxM = *std::max_element(c->M.begin(), c->M.end());
     v.atom_pos = d_pos; v.atom_rad = d_rad; v.atom_M = d_aM; v.atom_species = d_asp; v.atom_moff = d_amoff;
     v.atom_mat_off = d_amat; v.atom_tile_beg = d_tb; v.atom_tile_end = d_te; v.species_coul_off = d_coff; v.species_M = d_spM;
-    v.tiles = dt; v.pt_idx = d_idx; v.pt_u = d_u; v.seg_T = d_segT; v.seg_phase = d_segph;
+    v.tiles = dt; v.pt_idx = d_idx; v.pt_u = d_u; v.pt_first = d_first; v.seg_T = d_segT; v.seg_phase = d_segph;
+    c->h_coul_set.assign(nspecies, 0);
+    c->h_fixU.assign(natoms, std::nan(""));
     v.coul = d_coul; v.coul_set = d_cset; v.fixU = d_fu; v.fixJ = d_fj;
     // ---- work buffers ----
     const int rowsP = c->nk * c->ns;
@@ -451,6 +469,7 @@ dftu_status dftu_coulomb_integrals(dftu_handle h, int species, double* V_out) {
     if (rc != DFTU_OK) return (dftu_status)rc;
     int one = 1;
     cudaError_t e = cudaMemcpy(const_cast<int*>(c->v.coul_set) + species, &one, sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) c->h_coul_set[species] = 1;
     const int M = c->M[atom];
     if (e == cudaSuccess && V_out) e = cudaMemcpy(V_out, dst, (size_t)M * M * M * M * sizeof(double), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "coulomb_integrals");
@@ -471,6 +490,7 @@ dftu_status dftu_set_coulomb(dftu_handle h, int species, const double* V) {
     int one = 1;
     if (e == cudaSuccess) e = cudaMemcpy(const_cast<int*>(c->v.coul_set) + species, &one, sizeof(int), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(c, e, "set_coulomb");
+    c->h_coul_set[species] = 1;
     return DFTU_OK;
 }
 
@@ -485,6 +505,7 @@ dftu_status dftu_set_u(dftu_handle h, int atom, double U, double J) {
     cudaError_t e = cudaMemcpy(const_cast<double*>(c->v.fixU) + atom, &U, sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(const_cast<double*>(c->v.fixJ) + atom, &J, sizeof(double), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(c, e, "set_u");
+    c->h_fixU[atom] = U;
     return DFTU_OK;
 }
 
@@ -545,15 +566,11 @@ dftu_status dftu_acbn0_uj(dftu_handle h, dftu_stream stream) {
     if (!c) return DFTU_ERR_INVALID_ARG;
     if (!c->occ_ready) return fail(c, DFTU_ERR_NOT_READY, "acbn0_uj: call dftu_occupations first");
     Guard g(c->device);
-    std::vector<int> cset(c->nspecies);
-    std::vector<double> fu(c->atoms.size());
-    cudaError_t e = cudaMemcpy(cset.data(), c->v.coul_set, cset.size() * sizeof(int), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(fu.data(), c->v.fixU, fu.size() * sizeof(double), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_fail(c, e, "acbn0_uj");
     for (size_t a = 0; a < c->atoms.size(); ++a)
-        if (std::isnan(fu[a]) && !cset[c->atoms[a].species])
+        if (std::isnan(c->h_fixU[a]) && !c->h_coul_set[c->atoms[a].species])
             return fail(c, DFTU_ERR_NOT_READY, "acbn0_uj: Coulomb integrals of species " + std::to_string(c->atoms[a].species) +
                                                    " not set (dftu_coulomb_integrals or dftu_set_coulomb), and no fixed U");
+    cudaError_t e;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     e = launch_acbn0(c->v, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "acbn0_uj");
@@ -563,7 +580,7 @@ dftu_status dftu_acbn0_uj(dftu_handle h, dftu_stream stream) {
 }
 
 dftu_status dftu_apply(dftu_handle h, void* psi_out, dftu_prec prec, int nbands, int64_t ld_band, const double* coef,
-                       dftu_stream stream) {
+                       int accumulate, dftu_stream stream) {
     Ctx* c = reinterpret_cast<Ctx*>(h);
     if (!c) return DFTU_ERR_INVALID_ARG;
     if (!c->pot_ready || !c->proj_ready) return fail(c, DFTU_ERR_NOT_READY, "apply: call dftu_project and dftu_acbn0_uj first");
@@ -574,9 +591,45 @@ dftu_status dftu_apply(dftu_handle h, void* psi_out, dftu_prec prec, int nbands,
     strides(c, nbands, ld_band, sk, ss, sn);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = launch_apply(c->v, psi_out, prec, c->f64_mode, nbands, sk, ss, sn, coef ? coef : c->d_coef_one,
-                                 c->d_color_order, c->color_beg, c->variant[prec == DFTU_C64 ? 3 : 2], st);
+                                 c->d_color_order, c->color_beg, c->variant[prec == DFTU_C64 ? 3 : 2], accumulate ? 1 : 0, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "apply");
     c->last_stream = st;
+    return DFTU_OK;
+}
+
+dftu_status dftu_taylor_step(dftu_handle h, void* psi, void* work, dftu_prec prec, int nbands, int64_t ld_band,
+                             const double* f, double dt, int order, dftu_stream stream) {
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c) return DFTU_ERR_INVALID_ARG;
+    if (!c->atoms_ready) return fail(c, DFTU_ERR_NOT_READY, "taylor_step: call dftu_setup_atoms first");
+    if (!psi || !work || psi == work || !f || (prec != DFTU_C128 && prec != DFTU_C64) || !valid_stride_args(c, nbands, ld_band) ||
+        order < 1 || order > MAX_TAYLOR || !std::isfinite(dt))
+        return fail(c, DFTU_ERR_INVALID_ARG, "taylor_step: null or aliased buffers, bad precision, band count, order or dt");
+    for (size_t a = 0; a < c->atoms.size(); ++a)
+        if (std::isnan(c->h_fixU[a]) && !c->h_coul_set[c->atoms[a].species])
+            return fail(c, DFTU_ERR_NOT_READY, "taylor_step: Coulomb integrals missing for an ACBN0 atom");
+    Guard g(c->device);
+    int64_t sk, ss, sn;
+    strides(c, nbands, ld_band, sk, ss, sn);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int vp = c->variant[prec == DFTU_C64 ? 1 : 0], va = c->variant[prec == DFTU_C64 ? 3 : 2];
+    cudaError_t e = launch_project(c->v, psi, prec, c->f64_mode, nbands, sk, ss, sn, vp, st);
+    if (e == cudaSuccess) e = launch_nbar(c->v, nbands, st);
+    if (e == cudaSuccess) e = launch_occupations(c->v, f, nbands, st);
+    if (e == cudaSuccess) e = launch_acbn0(c->v, st);
+    if (e == cudaSuccess) e = launch_taylor_coefs(dt, order, c->d_taylor, st);
+    for (int j = 1; j <= order && e == cudaSuccess; ++j) {
+        const double* cj = c->d_taylor + 2 * (j - 1);
+        // term_j = (-i dt / j) V_U term_{j-1}, from the projections of term_{j-1} held by the handle
+        e = launch_apply(c->v, work, prec, c->f64_mode, nbands, sk, ss, sn, cj, c->d_color_order, c->color_beg, va, 0, st);
+        if (e == cudaSuccess)
+            e = launch_apply(c->v, psi, prec, c->f64_mode, nbands, sk, ss, sn, cj, c->d_color_order, c->color_beg, va, 1, st);
+        if (e == cudaSuccess && j < order) e = launch_project(c->v, work, prec, c->f64_mode, nbands, sk, ss, sn, vp, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "taylor_step");
+    c->last_stream = st;
+    c->proj_ready = c->occ_ready = c->pot_ready = true;
+    c->proj_nbands = nbands;
     return DFTU_OK;
 }
 

@@ -15,6 +15,7 @@ struct ApplyArgs {
     int nbands;
     const double* coef;   // device complex, never null (the handle supplies 1)
     const int* tile_list;  // tiles of this colour
+    int accumulate;        // 1: psi += c V_U psi_proj ; 0: psi = c V_U psi_proj on the sphere points
 };
 
 enum APol { A_F64 = 0, A_PAIR = 1, A_F32 = 2 };
@@ -80,7 +81,8 @@ __device__ __forceinline__ double pair_to_double(float h, float l, int sc) {
 // up to Q*U past the tile are staged as zeros, so the arithmetic needs no bounds test.
 template <int POL, int Q, int M, int U>
 __device__ __forceinline__ void apply_body(const Tile& t, const ApplyArgs& a, int64_t off, int q, int bl, const int* s_idx,
-                                           const unsigned char* after_idx, const unsigned char* after_c, int pe) {
+                                           const unsigned char* s_first, const unsigned char* after_idx,
+                                           const unsigned char* after_c, int pe) {
     if (POL == A_F64) {
         double2* row = reinterpret_cast<double2*>(a.psi) + off;
         const double* s_phi = reinterpret_cast<const double*>(after_c);
@@ -93,7 +95,7 @@ __device__ __forceinline__ void apply_body(const Tile& t, const ApplyArgs& a, in
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 int i = i0 + u * Q;
-                x[u] = (i < t.np) ? row[s_idx[i]] : make_double2(0.0, 0.0);
+                x[u] = (i < t.np && (a.accumulate || !s_first[i])) ? row[s_idx[i]] : make_double2(0.0, 0.0);
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -137,7 +139,7 @@ __device__ __forceinline__ void apply_body(const Tile& t, const ApplyArgs& a, in
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 int i = i0 + u * Q;
-                x[u] = (i < t.np) ? row[s_idx[i]] : make_double2(0.0, 0.0);
+                x[u] = (i < t.np && (a.accumulate || !s_first[i])) ? row[s_idx[i]] : make_double2(0.0, 0.0);
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -193,7 +195,7 @@ __device__ __forceinline__ void apply_body(const Tile& t, const ApplyArgs& a, in
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 int i = i0 + u * Q;
-                x[u] = (i < t.np) ? row[s_idx[i]] : make_float2(0.f, 0.f);
+                x[u] = (i < t.np && (a.accumulate || !s_first[i])) ? row[s_idx[i]] : make_float2(0.f, 0.f);
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -221,6 +223,7 @@ __global__ void __launch_bounds__(CTA, 3) k_apply(View v, ApplyArgs a) {
     constexpr int BPW = 32 / Q;
     constexpr int BPC = (CTA / 32) * BPW;
     __shared__ int s_pe;
+    __shared__ unsigned char s_first[TILE];
     const Tile t = v.tiles[a.tile_list[blockIdx.x]];
     const int ks = blockIdx.z;
     const int k = ks / v.ns, s = ks % v.ns;
@@ -231,7 +234,10 @@ __global__ void __launch_bounds__(CTA, 3) k_apply(View v, ApplyArgs a) {
 
     // ---- stage the tile once: grid indices and orbital rows (+ the orbitals' exponent bound)
     if (threadIdx.x == 0) s_pe = -200;
-    for (int i = threadIdx.x; i < TILE; i += CTA) s_idx[i] = (i < t.np) ? v.pt_idx[t.p0 + i] : 0;
+    for (int i = threadIdx.x; i < TILE; i += CTA) {
+        s_idx[i] = (i < t.np) ? v.pt_idx[t.p0 + i] : 0;
+        s_first[i] = (i < t.np) ? v.pt_first[t.p0 + i] : 0;
+    }
     __syncthreads();
     if (POL == A_F64) {
         double* s_phi = reinterpret_cast<double*>(after_c);
@@ -301,10 +307,10 @@ __global__ void __launch_bounds__(CTA, 3) k_apply(View v, ApplyArgs a) {
             const int64_t off = (int64_t)k * a.sk + (int64_t)s * a.ss + (int64_t)band * a.sn;
             const int pe = s_pe;
             switch (M) {
-                case 1: apply_body<POL, Q, 1, U>(t, a, off, q, bl, s_idx, after_idx, after_c, pe); break;
-                case 3: apply_body<POL, Q, 3, U>(t, a, off, q, bl, s_idx, after_idx, after_c, pe); break;
-                case 5: apply_body<POL, Q, 5, U>(t, a, off, q, bl, s_idx, after_idx, after_c, pe); break;
-                default: apply_body<POL, Q, 7, U>(t, a, off, q, bl, s_idx, after_idx, after_c, pe); break;
+                case 1: apply_body<POL, Q, 1, U>(t, a, off, q, bl, s_idx, s_first, after_idx, after_c, pe); break;
+                case 3: apply_body<POL, Q, 3, U>(t, a, off, q, bl, s_idx, s_first, after_idx, after_c, pe); break;
+                case 5: apply_body<POL, Q, 5, U>(t, a, off, q, bl, s_idx, s_first, after_idx, after_c, pe); break;
+                default: apply_body<POL, Q, 7, U>(t, a, off, q, bl, s_idx, s_first, after_idx, after_c, pe); break;
             }
         }
     }
@@ -315,7 +321,9 @@ static cudaError_t run_apply(const View& v, ApplyArgs a, const int* color_order,
                              cudaStream_t st) {
     constexpr int BPC = (CTA / 32) * (32 / Q);
     size_t smem = TILE * sizeof(int) + BPC * MAXM * 16 + (size_t)TILE_PAD * v.maxM * (POL == A_F64 ? sizeof(double) : sizeof(float4));
-    cudaError_t e = cudaFuncSetAttribute(k_apply<POL, Q, NBG, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaSuccess;
+    if (!smem_configured((const void*)k_apply<POL, Q, NBG, U>, (int)smem))
+        e = cudaFuncSetAttribute(k_apply<POL, Q, NBG, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     for (size_t c = 0; c + 1 < color_beg.size(); ++c) {
         int n = color_beg[c + 1] - color_beg[c];
@@ -331,8 +339,8 @@ static cudaError_t run_apply(const View& v, ApplyArgs a, const int* color_order,
 
 cudaError_t launch_apply(const View& v, void* psi, dftu_prec prec, dftu_f64_mode mode, int nbands,
                          int64_t sk, int64_t ss, int64_t sn, const double* coef, const int* color_order,
-                         const std::vector<int>& color_beg, int variant, cudaStream_t st) {
-    ApplyArgs a{psi, sk, ss, sn, nbands, coef, nullptr};
+                         const std::vector<int>& color_beg, int variant, int accumulate, cudaStream_t st) {
+    ApplyArgs a{psi, sk, ss, sn, nbands, coef, nullptr, accumulate};
     if (prec == DFTU_C64) {
         switch (variant) {   // (lanes per band, band groups per CTA, points in flight per lane)
             case 1: return run_apply<A_F32, 8, 4, 4>(v, a, color_order, color_beg, st);
@@ -348,6 +356,17 @@ cudaError_t launch_apply(const View& v, void* psi, dftu_prec prec, dftu_f64_mode
         case 3: return run_apply<A_PAIR, 8, 4, 8>(v, a, color_order, color_beg, st);
         default: return run_apply<A_PAIR, 8, 4, 4>(v, a, color_order, color_beg, st);
     }
+}
+
+// Taylor coefficients of exp(-i dt H): term j = (-i dt / j) H term_{j-1}.
+__global__ void k_taylor_coefs(double dt, int order, double2* c) {
+    int j = threadIdx.x + 1;
+    if (j <= order) c[j - 1] = make_double2(0.0, -dt / (double)j);
+}
+
+cudaError_t launch_taylor_coefs(double dt, int order, double* coefs, cudaStream_t st) {
+    k_taylor_coefs<<<1, MAX_TAYLOR, 0, st>>>(dt, order, reinterpret_cast<double2*>(coefs));
+    return cudaGetLastError();
 }
 
 }  // namespace dftu

@@ -16,6 +16,7 @@ constexpr int MAXM = 7;        // orbitals per shell, l <= 3
 constexpr int IMG_RANGE = 2;   // lattice images |T| <= 2 cells per axis
 constexpr int NIMG = 125;      // (2*IMG_RANGE+1)^3 image ids
 constexpr int CTA = 256;       // threads per CTA of the streaming kernels
+constexpr int MAX_TAYLOR = 8;  // highest Taylor order of dftu_taylor_step
 
 enum StatusBits : int { ST_NONFINITE = 1, ST_ZERO_DENOM = 2, ST_TIMEOUT = 4 };
 
@@ -63,6 +64,7 @@ struct View {
     const Tile* tiles;
     const int* pt_idx;     // [S] wrapped linear index, GPU order
     const int* pt_u;       // [S][3] unfolded integer coordinates, GPU order
+    const unsigned char* pt_first;   // [S] 1 if no tile of an earlier apply colour covers this grid point
     double* phi64;         // [sum S_I M_I]
     float* phi_hi;
     float* phi_lo;
@@ -116,6 +118,9 @@ struct Ctx {
     std::vector<void*> allocs;   // every device allocation, freed by dftu_destroy
     int* d_color_order = nullptr;
     double* d_coef_one = nullptr;
+    double* d_taylor = nullptr;      // [MAX_TAYLOR] complex Taylor coefficients -i dt / j
+    std::vector<int> h_coul_set;     // host copies, so hot-path calls never read the device
+    std::vector<double> h_fixU;
 };
 
 // ---- launchers implemented in the .cu files (all asynchronous on `st`) -------------------------
@@ -135,7 +140,11 @@ cudaError_t launch_occupations(const View& v, const double* f, int nbands, cudaS
 cudaError_t launch_acbn0(const View& v, cudaStream_t st);
 cudaError_t launch_apply(const View& v, void* psi, dftu_prec prec, dftu_f64_mode mode, int nbands,
                          int64_t sk, int64_t ss, int64_t sn, const double* coef, const int* color_order,
-                         const std::vector<int>& color_beg, int variant, cudaStream_t st);
+                         const std::vector<int>& color_beg, int variant, int accumulate, cudaStream_t st);
+cudaError_t launch_taylor_coefs(double dt, int order, double* coefs, cudaStream_t st);
+
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per kernel and device, never inside a capture.
+bool smem_configured(const void* fn, int bytes);
 
 // Coulomb integrals of one atom's orbitals (blocking); W_out [P][P] with P = M(M+1)/2 pair index.
 int coulomb_atom(const View& v, const Ctx& c, int atom, double* V_dev, std::string& err);

@@ -17,6 +17,9 @@
 //          in a second float.  Chains are merged with TwoSum.  Accuracy ~2^-44 of the chain scale.
 //   F32  : complex64 states, FP32 orbitals hi + lo, FP32 chunk sums merged with TwoSum per lane,
 //          FP64 across tiles.
+#include <mutex>
+#include <utility>
+
 #include "dftu_internal.cuh"
 
 namespace dftu {
@@ -356,6 +359,23 @@ __global__ void __launch_bounds__(CTA, 2) k_project(View v, ProjArgs a) {
     }
 }
 
+// One record per (kernel, device): the largest dynamic shared memory size already allowed.
+bool smem_configured(const void* fn, int bytes) {
+    static std::mutex mu;
+    static std::vector<std::pair<std::pair<const void*, int>, int>> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    for (auto& d : done)
+        if (d.first.first == fn && d.first.second == dev) {
+            if (d.second >= bytes) return true;
+            d.second = bytes;
+            return false;
+        }
+    done.push_back({{fn, dev}, bytes});
+    return false;
+}
+
 // p[ks][band][moff_I + m] = sum over the atom's tiles (fixed order) of the tile partials.
 __global__ void k_tile_reduce(View v, int nbands) {
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -382,7 +402,9 @@ template <int POL, int Q, int CH, int NBG>
 static cudaError_t run_project(const View& v, const ProjArgs& a, cudaStream_t st) {
     static_assert(Q * CH <= TILE_PAD - TILE, "chained loops read up to Q*CH rows past the tile");
     size_t smem = TILE * sizeof(int) + (size_t)TILE_PAD * v.maxM * (POL == P_F64 ? sizeof(double) : sizeof(float4));
-    cudaError_t e = cudaFuncSetAttribute(k_project<POL, Q, CH, NBG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaSuccess;
+    if (!smem_configured((const void*)k_project<POL, Q, CH, NBG>, (int)smem))
+        e = cudaFuncSetAttribute(k_project<POL, Q, CH, NBG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     constexpr int BPC = (CTA / 32) * (32 / Q);
     dim3 grid(v.ntiles, (a.nbands + BPC * NBG - 1) / (BPC * NBG), v.nk * v.ns);

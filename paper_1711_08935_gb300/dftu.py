@@ -30,7 +30,8 @@ EXPORTED = ["dftu_create", "dftu_setup_atoms", "dftu_get_sphere", "dftu_coulomb_
             "dftu_set_u", "dftu_set_f64_mode", "dftu_project", "dftu_occupations", "dftu_acbn0_uj", "dftu_apply",
             "dftu_get_results", "dftu_get_renormalized", "dftu_get_projections", "dftu_total_orbitals",
             "dftu_atom_points", "dftu_sync_status", "dftu_last_error", "dftu_destroy",
-            "dftu_set_kernel_variant", "dftu_kernel_variants", "dftu_project_sphere_noalloc"]
+            "dftu_set_kernel_variant", "dftu_kernel_variants", "dftu_project_sphere_noalloc",
+            "dftu_taylor_step"]
 
 
 class DftuGrid(C.Structure):
@@ -74,7 +75,8 @@ def load() -> C.CDLL:
         "dftu_project": [vp, vp, i32, i32, i64, vp],
         "dftu_occupations": [vp, vp, vp],
         "dftu_acbn0_uj": [vp, vp],
-        "dftu_apply": [vp, vp, i32, i32, i64, vp, vp],
+        "dftu_apply": [vp, vp, i32, i32, i64, vp, i32, vp],
+        "dftu_taylor_step": [vp, vp, vp, i32, i32, i64, vp, d, i32, vp],
         "dftu_get_results": [vp, dp, dp, dp, dp, dp, vp],
         "dftu_get_renormalized": [vp, dp, dp, vp],
         "dftu_get_projections": [vp, dp, vp],
@@ -130,6 +132,7 @@ class Handle:
         self.M = []
         self.species = []
         self.natoms = 0
+        self._variants = [0, 0, 0, 0]
 
     # ------------------------------------------------------------------ plumbing
     def _check(self, status: int, h=-1):
@@ -191,6 +194,11 @@ class Handle:
 
     def set_kernel_variant(self, which: int, variant: int):
         self._check(self.lib.dftu_set_kernel_variant(self.h, which, variant))
+        self._variants[which] = variant
+
+    def variants_now(self):
+        """Kernel variants in use: (project c128, project c64, apply c128, apply c64)."""
+        return tuple(self._variants)
 
     # ------------------------------------------------------------------ hot path
     def _psi_args(self, psi: torch.Tensor):
@@ -226,14 +234,24 @@ class Handle:
     def acbn0_uj(self, stream=None):
         self._check(self.lib.dftu_acbn0_uj(self.h, _stream_ptr(stream, self.device)))
 
-    def apply(self, psi: torch.Tensor, coef: Optional[torch.Tensor] = None, stream=None):
+    def apply(self, psi: torch.Tensor, coef: Optional[torch.Tensor] = None, accumulate: bool = True, stream=None):
         prec, nb, ld = self._psi_args(psi)
         cp = None
         if coef is not None:
             if coef.dtype != torch.complex128 or not coef.is_cuda:
                 raise ValueError("coef must be a complex128 CUDA tensor")
             cp = C.c_void_p(coef.data_ptr())
-        self._check(self.lib.dftu_apply(self.h, C.c_void_p(psi.data_ptr()), prec, nb, ld, cp, _stream_ptr(stream, self.device)))
+        self._check(self.lib.dftu_apply(self.h, C.c_void_p(psi.data_ptr()), prec, nb, ld, cp, 1 if accumulate else 0,
+                                        _stream_ptr(stream, self.device)))
+
+    def taylor_step(self, psi: torch.Tensor, work: torch.Tensor, f: torch.Tensor, dt: float, order: int = 4, stream=None):
+        prec, nb, ld = self._psi_args(psi)
+        if work.shape != psi.shape or work.dtype != psi.dtype or not work.is_contiguous():
+            raise ValueError("work must match psi")
+        if f.dtype != torch.float64 or not f.is_cuda or not f.is_contiguous():
+            raise ValueError("f must be a contiguous float64 CUDA tensor")
+        self._check(self.lib.dftu_taylor_step(self.h, C.c_void_p(psi.data_ptr()), C.c_void_p(work.data_ptr()), prec, nb, ld,
+                                              C.c_void_p(f.data_ptr()), float(dt), int(order), _stream_ptr(stream, self.device)))
 
     # ------------------------------------------------------------------ results
     def _mat_sizes(self):

@@ -39,3 +39,14 @@ def gram_schmidt_after(first: np.ndarray, rest: np.ndarray, dV: float) -> np.nda
             A[i] -= dV * np.vdot(A[j], A[i]) * A[j]
         A[i] /= math.sqrt(dV * np.vdot(A[i], A[i]).real)
     return A
+
+
+def overlapping_three_atoms():
+    """Periodic 24^3 cell (h = 0.4, L = 9.6) with three atoms of three species whose spheres overlap
+    each other (and one reaches its own periodic image): the apply must add every contribution."""
+    g = Grid(n=(24, 24, 24), h=(0.4, 0.4, 0.4), periodic=True)
+    at = [Atom((1.0, 1.2, 0.8), 0, 2, 3.2), Atom((3.1, 2.0, 1.5), 1, 1, 2.8), Atom((2.0, 3.6, 2.9), 2, 2, 5.0)]
+    kp = np.array([[0.11, -0.05, 0.2], [-0.2, 0.13, 0.04]])
+    return System(g, at, [synth.hydrogenic_radial(3, 2, 3.0), synth.hydrogenic_radial(2, 1, 3.5),
+                          synth.hydrogenic_radial(3, 2, 2.5)], kp, np.array([0.5, 0.5]), nspin=1,
+                  name="overlapping spheres, three species, 2 k")
