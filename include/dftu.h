@@ -186,6 +186,35 @@ dftu_status dftu_project_sphere_noalloc(const void* psi, dftu_prec prec, int nba
                                         const int32_t* idx, const double* phase, const double* phi, int npts,
                                         int M, double dV, double* p_out, dftu_stream stream);
 
+/* ---- Batches of independent systems -------------------------------------------------------------
+ * Many small systems (e.g. molecules with their own isolated grids) in one context: every member is an
+ * ordinary handle that went through dftu_create/dftu_setup_atoms (and Coulomb integrals or fixed U), all
+ * on one device.  The batch launches ONE persistent projection kernel and ONE persistent apply kernel
+ * per apply colour over the tiles of all members: every CTA takes (system, tile, k*spin) work items from
+ * an atomic counter until the list is exhausted, so uneven systems balance themselves.  The small
+ * per-system steps (Nbar, occupations, U/J, potential) run as single batched launches.  Results are
+ * read per member with the handle calls above (dftu_get_results etc.); the arithmetic is that of the
+ * single-system calls, in the same order per member.  The paper has no counterpart for the batching;
+ * it packages Eqs. (4)-(11) for many systems at once. */
+typedef struct dftu_batch_ctx* dftu_batch;
+
+/* systems: host array of nsys set-up handles (not owned; they must outlive the batch). */
+dftu_status dftu_batch_create(dftu_batch* out, int nsys, const dftu_handle* systems);
+
+/* Bind the members' states and occupations (host arrays of nsys entries): psi[s] device states in the
+ * member's layout with nbands[s] bands and ld_band[s] elements per band, f[s] device occupations as for
+ * dftu_occupations.  One precision for the whole batch.  Copies a small pointer table to the device. */
+dftu_status dftu_batch_bind(dftu_batch b, const void* const* psi, dftu_prec prec, const int* nbands,
+                            const int64_t* ld_band, const double* const* f);
+
+dftu_status dftu_batch_project(dftu_batch b, dftu_stream stream);
+dftu_status dftu_batch_occupations(dftu_batch b, dftu_stream stream);
+dftu_status dftu_batch_acbn0_uj(dftu_batch b, dftu_stream stream);
+/* coef: device complex FP64 or NULL for 1; accumulate as for dftu_apply.  Writes the bound states. */
+dftu_status dftu_batch_apply(dftu_batch b, const double* coef, int accumulate, dftu_stream stream);
+const char* dftu_batch_last_error(dftu_batch b);
+void dftu_batch_destroy(dftu_batch b);
+
 /* Results to host memory (blocking on stream).  Any pointer may be NULL.
  *   n_out     [atom][spin][M][M] interleaved complex (paper's n, Eq. 4); non-collinear [atom][2M][2M]
  *             with index (component*M + m); atoms packed one after another with their own M.

@@ -5,6 +5,8 @@
 // lanes read-modify-writes its band's points.  Tiles are launched colour by colour: tiles of one
 // colour touch disjoint grid points, so a point shared by several spheres (or by periodic images
 // of one sphere) is updated by successive launches in a fixed order, without atomics.
+#include <algorithm>
+
 #include "dftu_internal.cuh"
 
 namespace dftu {
@@ -215,17 +217,15 @@ __device__ __forceinline__ void apply_body(const Tile& t, const ApplyArgs& a, in
     }
 }
 
+// One work item: tile `tile_id` (a tile of the current colour) of the system (v, a), component ks, band chunk `chunk`.
 template <int POL, int Q, int NBG, int U>
-__global__ void __launch_bounds__(CTA, 3) k_apply(View v, ApplyArgs a) {
+__device__ __forceinline__ void apply_item(const View& v, const ApplyArgs& a, int tile_id, int ks, int chunk,
+                                           unsigned char* smem, int& s_pe, unsigned char* s_first) {
     static_assert(Q * U <= TILE_PAD - TILE, "batched loops read up to Q*U rows past the tile");
-    extern __shared__ __align__(16) unsigned char smem[];
     int* s_idx = reinterpret_cast<int*>(smem);
     constexpr int BPW = 32 / Q;
     constexpr int BPC = (CTA / 32) * BPW;
-    __shared__ int s_pe;
-    __shared__ unsigned char s_first[TILE];
-    const Tile t = v.tiles[a.tile_list[blockIdx.x]];
-    const int ks = blockIdx.z;
+    const Tile t = v.tiles[tile_id];
     const int k = ks / v.ns, s = ks % v.ns;
     const int M = t.M;
     unsigned char* after_idx = smem + TILE * sizeof(int);
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(CTA, 3) k_apply(View v, ApplyArgs a) {
     const int mo = v.atom_moff[t.atom];
     const int64_t vo = v.atom_mat_off[t.atom];
     for (int g = 0; g < NBG; ++g) {
-        const int band0 = (blockIdx.y * NBG + g) * BPC;
+        const int band0 = (chunk * NBG + g) * BPC;
         if (band0 >= a.nbands) break;
         __syncthreads();   // staging done / previous group's readers done with the coefficient table
         if (threadIdx.x < BPC * M) {
@@ -317,6 +317,40 @@ __global__ void __launch_bounds__(CTA, 3) k_apply(View v, ApplyArgs a) {
 }
 
 template <int POL, int Q, int NBG, int U>
+__global__ void __launch_bounds__(CTA, 3) k_apply(View v, ApplyArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_pe;
+    __shared__ unsigned char s_first[TILE];
+    apply_item<POL, Q, NBG, U>(v, a, a.tile_list[blockIdx.x], blockIdx.z, blockIdx.y, smem, s_pe, s_first);
+}
+
+// Persistent form over many systems: (system, tile, k*spin) items of one colour from a counter.
+template <int POL, int Q, int NBG, int U>
+__global__ void __launch_bounds__(CTA, 3) k_apply_batch(const View* __restrict__ views, const ProjArgs* __restrict__ args,
+                                                        const int4* __restrict__ items, int nitems, int* counter,
+                                                        const double* coef, int accumulate) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_pe, s_item;
+    __shared__ unsigned char s_first[TILE];
+    constexpr int BPC = (CTA / 32) * (32 / Q);
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems) break;
+        const int4 w = items[it];
+        const View& v = views[w.x];
+        const ProjArgs& pa = args[w.x];
+        ApplyArgs a{const_cast<void*>(pa.psi), pa.sk, pa.ss, pa.sn, pa.nbands, coef, nullptr, accumulate};
+        const int nchunks = (pa.nbands + BPC * NBG - 1) / (BPC * NBG);
+        for (int c = 0; c < nchunks; ++c) {
+            apply_item<POL, Q, NBG, U>(v, a, w.y, w.z, c, smem, s_pe, s_first);
+            __syncthreads();
+        }
+    }
+}
+
+template <int POL, int Q, int NBG, int U>
 static cudaError_t run_apply(const View& v, ApplyArgs a, const int* color_order, const std::vector<int>& color_beg,
                              cudaStream_t st) {
     constexpr int BPC = (CTA / 32) * (32 / Q);
@@ -367,6 +401,51 @@ __global__ void k_taylor_coefs(double dt, int order, double2* c) {
 cudaError_t launch_taylor_coefs(double dt, int order, double* coefs, cudaStream_t st) {
     k_taylor_coefs<<<1, MAX_TAYLOR, 0, st>>>(dt, order, reinterpret_cast<double2*>(coefs));
     return cudaGetLastError();
+}
+
+template <int POL, int Q, int NBG, int U>
+static cudaError_t run_apply_batch(const BatchLaunch& b, const double* coef, int accumulate, cudaStream_t st) {
+    constexpr int BPC = (CTA / 32) * (32 / Q);
+    size_t smem = TILE * sizeof(int) + BPC * MAXM * 16 + (size_t)TILE_PAD * b.maxM * (POL == A_F64 ? sizeof(double) : sizeof(float4));
+    auto fn = k_apply_batch<POL, Q, NBG, U>;
+    cudaError_t e = cudaSuccess;
+    if (!smem_configured((const void*)fn, (int)smem)) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, nsm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, CTA, smem);
+    if (e != cudaSuccess) return e;
+    for (size_t c = 0; c + 1 < b.color_beg.size(); ++c) {
+        int n = b.color_beg[c + 1] - b.color_beg[c];
+        if (n == 0) continue;
+        e = cudaMemsetAsync(b.counter, 0, sizeof(int), st);
+        if (e != cudaSuccess) return e;
+        int grid = std::max(1, std::min(per_sm * nsm, n));
+        fn<<<grid, CTA, smem, st>>>(b.views, b.args, b.color_items + b.color_beg[c], n, b.counter, coef, accumulate);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_apply_batch(const BatchLaunch& b, dftu_prec prec, dftu_f64_mode mode, int variant, const double* coef,
+                               int accumulate, cudaStream_t st) {
+    if (prec == DFTU_C64) {
+        switch (variant) {
+            case 1: return run_apply_batch<A_F32, 8, 4, 4>(b, coef, accumulate, st);
+            case 2: return run_apply_batch<A_F32, 4, 4, 8>(b, coef, accumulate, st);
+            case 3: return run_apply_batch<A_F32, 16, 4, 4>(b, coef, accumulate, st);
+            default: return run_apply_batch<A_F32, 8, 4, 8>(b, coef, accumulate, st);
+        }
+    }
+    if (mode == DFTU_F64_NATIVE) return run_apply_batch<A_F64, 8, 4, 4>(b, coef, accumulate, st);
+    switch (variant) {
+        case 1: return run_apply_batch<A_PAIR, 8, 4, 2>(b, coef, accumulate, st);
+        case 2: return run_apply_batch<A_PAIR, 4, 4, 4>(b, coef, accumulate, st);
+        case 3: return run_apply_batch<A_PAIR, 8, 4, 8>(b, coef, accumulate, st);
+        default: return run_apply_batch<A_PAIR, 8, 4, 4>(b, coef, accumulate, st);
+    }
 }
 
 }  // namespace dftu

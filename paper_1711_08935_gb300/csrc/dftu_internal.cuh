@@ -123,6 +123,31 @@ struct Ctx {
     std::vector<double> h_fixU;
 };
 
+// Arguments of a streaming kernel for one system's states: base pointer, element strides of k, spin (or
+// spinor component) and band, and the number of bands.
+struct ProjArgs {
+    const void* psi;
+    int64_t sk, ss, sn;
+    int nbands;
+};
+
+// Device tables of a batch of systems for the persistent kernels.
+struct BatchLaunch {
+    const View* views;        // [nsys]
+    const ProjArgs* args;     // [nsys]
+    const double* const* f;   // [nsys] occupations, device pointers
+    const int4* items;        // (system, tile, k*spin, 0) work items, all tiles
+    int nitems;
+    const int4* color_items;  // work items of the apply, grouped by colour
+    std::vector<int> color_beg;
+    int* counter;             // work-queue counter (reset before each persistent launch)
+    int nsys;
+    int maxM;
+    int64_t max_reduce;       // max over systems of (k*spin rows) * nbands * sum M
+    int max_rows_nbar;        // max over systems of rows * nbands for Nbar
+    int max_atoms, max_ns;
+};
+
 // ---- launchers implemented in the .cu files (all asynchronous on `st`) -------------------------
 cudaError_t launch_sphere_flags(const View& v, const double* pos, const double* rad, const int* box_lo,
                                 const int* box_dim, const int64_t* box_off, int natoms, int64_t nbox,
@@ -142,6 +167,11 @@ cudaError_t launch_apply(const View& v, void* psi, dftu_prec prec, dftu_f64_mode
                          int64_t sk, int64_t ss, int64_t sn, const double* coef, const int* color_order,
                          const std::vector<int>& color_beg, int variant, int accumulate, cudaStream_t st);
 cudaError_t launch_taylor_coefs(double dt, int order, double* coefs, cudaStream_t st);
+cudaError_t launch_project_batch(const BatchLaunch& b, dftu_prec prec, dftu_f64_mode mode, int variant, cudaStream_t st);
+cudaError_t launch_occupations_batch(const BatchLaunch& b, cudaStream_t st);
+cudaError_t launch_acbn0_batch(const BatchLaunch& b, cudaStream_t st);
+cudaError_t launch_apply_batch(const BatchLaunch& b, dftu_prec prec, dftu_f64_mode mode, int variant, const double* coef,
+                               int accumulate, cudaStream_t st);
 
 // cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per kernel and device, never inside a capture.
 bool smem_configured(const void* fn, int bytes);

@@ -11,8 +11,7 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ double2 cmulc(double2 a, double2 b) { return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y); }  // a conj(b)
 
 // Eq. (9): Nbar per state = sum over atoms of the state's species-mates and m (and spinor components) of |p|^2.
-__global__ void k_nbar(View v, int nbands) {
-    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void nbar_elem(const View& v, int nbands, int64_t g) {
     int rows = v.noncollinear ? v.nk : v.nk * v.ns;
     if (g >= (int64_t)rows * nbands) return;
     int row = (int)(g / nbands), band = (int)(g % nbands);
@@ -32,11 +31,15 @@ __global__ void k_nbar(View v, int nbands) {
     }
 }
 
+__global__ void k_nbar(View v, int nbands) { nbar_elem(v, nbands, (int64_t)blockIdx.x * blockDim.x + threadIdx.x); }
+
+__global__ void k_nbar_batch(const View* __restrict__ views, const ProjArgs* __restrict__ args) {
+    nbar_elem(views[blockIdx.y], args[blockIdx.y].nbands, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // Eqs. (4), (8), (A2), (B3): one CTA per (atom, spin channel) [collinear] or per atom [non-collinear].
 // Thread (pair, slice): pair = matrix element (a,b); slices split the (k, band) sum, reduced in order.
-__global__ void k_occupations(View v, const double* __restrict__ f, int nbands) {
-    const int a = blockIdx.x;
-    const int s = blockIdx.y;
+__device__ __forceinline__ void occupations_block(const View& v, const double* __restrict__ f, int nbands, int a, int s) {
     const int M = v.atom_M[a], mo = v.atom_moff[a], sp = v.atom_species[a];
     const int D = v.noncollinear ? 2 * M : M;
     const int P = D * D;
@@ -84,6 +87,16 @@ __global__ void k_occupations(View v, const double* __restrict__ f, int nbands) 
     }
 }
 
+__global__ void k_occupations(View v, const double* __restrict__ f, int nbands) {
+    occupations_block(v, f, nbands, blockIdx.x, blockIdx.y);
+}
+
+__global__ void k_occupations_batch(const View* __restrict__ views, const ProjArgs* __restrict__ args, const double* const* f) {
+    const View& v = views[blockIdx.z];
+    if ((int)blockIdx.x >= v.natoms || (int)blockIdx.y >= (v.noncollinear ? 1 : v.ns)) return;
+    occupations_block(v, f[blockIdx.z], args[blockIdx.z].nbands, blockIdx.x, blockIdx.y);
+}
+
 __device__ __forceinline__ double warp_sum(double x) {
     for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
     return x;
@@ -91,7 +104,7 @@ __device__ __forceinline__ double warp_sum(double x) {
 
 // Eqs. (10)-(11) [collinear/unpolarised] or (B5)-(B6) [non-collinear], then Eq. (3)/(A5) and Eq. (6).
 // One warp per atom; sums are lane-strided then tree-reduced (fixed order).
-__global__ void k_acbn0(View v) {
+__device__ __forceinline__ void acbn0_block(const View& v) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int a = warp; a < v.natoms; a += nw) {
         const int M = v.atom_M[a], sp = v.atom_species[a];
@@ -220,6 +233,10 @@ __global__ void k_acbn0(View v) {
     }
 }
 
+__global__ void __launch_bounds__(1024) k_acbn0(View v) { acbn0_block(v); }
+
+__global__ void __launch_bounds__(256) k_acbn0_batch(const View* __restrict__ views) { acbn0_block(views[blockIdx.x]); }
+
 cudaError_t launch_nbar(const View& v, int nbands, cudaStream_t st) {
     int rows = v.noncollinear ? v.nk : v.nk * v.ns;
     int64_t n = (int64_t)rows * nbands;
@@ -235,6 +252,21 @@ cudaError_t launch_occupations(const View& v, const double* f, int nbands, cudaS
 
 cudaError_t launch_acbn0(const View& v, cudaStream_t st) {
     k_acbn0<<<1, 1024, 0, st>>>(v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_occupations_batch(const BatchLaunch& b, cudaStream_t st) {
+    dim3 g1((unsigned)((b.max_rows_nbar + 255) / 256), b.nsys);
+    k_nbar_batch<<<g1, 256, 0, st>>>(b.views, b.args);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 g2(b.max_atoms, b.max_ns, b.nsys);
+    k_occupations_batch<<<g2, CTA, 0, st>>>(b.views, b.args, b.f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_acbn0_batch(const BatchLaunch& b, cudaStream_t st) {
+    k_acbn0_batch<<<b.nsys, 256, 0, st>>>(b.views);
     return cudaGetLastError();
 }
 

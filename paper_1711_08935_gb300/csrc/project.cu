@@ -17,6 +17,7 @@
 //          in a second float.  Chains are merged with TwoSum.  Accuracy ~2^-44 of the chain scale.
 //   F32  : complex64 states, FP32 orbitals hi + lo, FP32 chunk sums merged with TwoSum per lane,
 //          FP64 across tiles.
+#include <algorithm>
 #include <mutex>
 #include <utility>
 
@@ -57,12 +58,6 @@ __device__ __forceinline__ void write_partial(const View& v, const Tile& t, int 
     double2 r = make_double2(v.dV * (ph.x * re - ph.y * im), v.dV * (ph.x * im + ph.y * re));
     v.part[((int64_t)ks * v.max_bands + band) * v.TM + t.moff + m] = r;
 }
-
-struct ProjArgs {
-    const void* psi;
-    int64_t sk, ss, sn;
-    int nbands;
-};
 
 // ------------------------------------------------------------------------------------------------
 // F64 policy
@@ -288,19 +283,19 @@ __device__ __forceinline__ void proj_body_pair(const View& v, const Tile& t, int
 // ------------------------------------------------------------------------------------------------
 enum Pol { P_F64 = 0, P_PAIR = 1, P_F32 = 2 };
 
+// One work item: tile `tile_id` of the system described by (v, a), spin/component index ks, every band of
+// band chunk `chunk` (NBG groups of BPC bands).  The tile is staged in shared memory once.
 template <int POL, int Q, int CH, int NBG>
-__global__ void __launch_bounds__(CTA, 2) k_project(View v, ProjArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, int tile_id, int ks, int chunk,
+                                             unsigned char* smem, int* s_pe) {
     int* s_idx = reinterpret_cast<int*>(smem);
-    const Tile t = v.tiles[blockIdx.x];
-    const int ks = blockIdx.z;
+    const Tile t = v.tiles[tile_id];
     const int k = ks / v.ns, s = ks % v.ns;
     constexpr int BPW = 32 / Q;
     constexpr int BPC = (CTA / 32) * BPW;
 
     // ---- stage the tile once (grid indices, orbital rows, orbital exponent bound)
-    __shared__ int s_pe;
-    if (threadIdx.x == 0) s_pe = -200;
+    if (threadIdx.x == 0) *s_pe = -200;
     for (int i = threadIdx.x; i < TILE; i += CTA) s_idx[i] = (i < t.np) ? v.pt_idx[t.p0 + i] : 0;
     __syncthreads();
     if (POL == P_F64) {
@@ -316,13 +311,13 @@ __global__ void __launch_bounds__(CTA, 2) k_project(View v, ProjArgs a) {
             s_phi[e] = make_float4(hi, hi, lo, lo);
             if (hi != 0.f) pe = max(pe, ((__float_as_int(hi) >> 23) & 0xFF) - 127 + 1);   // |hi| < 2^pe
         }
-        if (POL == P_PAIR) atomicMax(&s_pe, pe);
+        if (POL == P_PAIR) atomicMax(s_pe, pe);
     }
     __syncthreads();
 
     // ---- stream NBG groups of BPC bands over the staged tile
     for (int g = 0; g < NBG; ++g) {
-        const int band0 = (blockIdx.y * NBG + g) * BPC;
+        const int band0 = (chunk * NBG + g) * BPC;
         if (band0 >= a.nbands) break;
         const int band = band0 + (threadIdx.x >> 5) * BPW + ((threadIdx.x & 31) / Q);
         const bool active = band < a.nbands;
@@ -339,7 +334,7 @@ __global__ void __launch_bounds__(CTA, 2) k_project(View v, ProjArgs a) {
         } else if (POL == P_PAIR) {
             const float4* s_phi = reinterpret_cast<const float4*>(smem + TILE * sizeof(int));
             const double2* row = active ? reinterpret_cast<const double2*>(a.psi) + off : nullptr;
-            const int pe = s_pe;
+            const int pe = *s_pe;
             switch (t.M) {
                 case 1: proj_body_pair<1, Q, CH>(v, t, ks, band, row, s_idx, s_phi, pe); break;
                 case 3: proj_body_pair<3, Q, CH>(v, t, ks, band, row, s_idx, s_phi, pe); break;
@@ -355,6 +350,37 @@ __global__ void __launch_bounds__(CTA, 2) k_project(View v, ProjArgs a) {
                 case 5: proj_body_f32<5, Q, CH>(v, t, ks, band, row, s_idx, s_phi); break;
                 default: proj_body_f32<7, Q, CH>(v, t, ks, band, row, s_idx, s_phi); break;
             }
+        }
+    }
+}
+
+template <int POL, int Q, int CH, int NBG>
+__global__ void __launch_bounds__(CTA, 2) k_project(View v, ProjArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_pe;
+    project_item<POL, Q, CH, NBG>(v, a, blockIdx.x, blockIdx.z, blockIdx.y, smem, &s_pe);
+}
+
+// Persistent form over many systems: every CTA takes (system, tile, k*spin) items from a counter until
+// the list is exhausted and processes all band chunks of the item's system.
+template <int POL, int Q, int CH, int NBG>
+__global__ void __launch_bounds__(CTA, 2) k_project_batch(const View* __restrict__ views, const ProjArgs* __restrict__ args,
+                                                          const int4* __restrict__ items, int nitems, int* counter) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_pe, s_item;
+    constexpr int BPC = (CTA / 32) * (32 / Q);
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems) break;
+        const int4 w = items[it];   // (system, tile, k*spin, unused)
+        const View& v = views[w.x];
+        const ProjArgs& a = args[w.x];
+        const int nchunks = (a.nbands + BPC * NBG - 1) / (BPC * NBG);
+        for (int c = 0; c < nchunks; ++c) {
+            project_item<POL, Q, CH, NBG>(v, a, w.y, w.z, c, smem, &s_pe);
+            __syncthreads();   // the next chunk or item restages shared memory
         }
     }
 }
@@ -377,8 +403,7 @@ bool smem_configured(const void* fn, int bytes) {
 }
 
 // p[ks][band][moff_I + m] = sum over the atom's tiles (fixed order) of the tile partials.
-__global__ void k_tile_reduce(View v, int nbands) {
-    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void tile_reduce_elem(const View& v, int nbands, int64_t g) {
     int64_t rows = (int64_t)v.nk * v.ns * nbands;
     if (g >= rows * v.MT) return;
     int64_t rowi = g / v.MT;
@@ -396,6 +421,14 @@ __global__ void k_tile_reduce(View v, int nbands) {
     }
     if (!isfinite(re) || !isfinite(im)) atomicOr(v.status, ST_NONFINITE);
     v.p[((int64_t)ks * v.max_bands + band) * v.MT + j] = make_double2(re, im);
+}
+
+__global__ void k_tile_reduce(View v, int nbands) {
+    tile_reduce_elem(v, nbands, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__global__ void k_tile_reduce_batch(const View* __restrict__ views, const ProjArgs* __restrict__ args) {
+    tile_reduce_elem(views[blockIdx.y], args[blockIdx.y].nbands, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 template <int POL, int Q, int CH, int NBG>
@@ -436,6 +469,50 @@ cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_
     if (e != cudaSuccess) return e;
     int64_t n = (int64_t)v.nk * v.ns * nbands * v.MT;
     k_tile_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(v, nbands);
+    return cudaGetLastError();
+}
+
+template <int POL, int Q, int CH, int NBG>
+static cudaError_t run_project_batch(const BatchLaunch& b, cudaStream_t st) {
+    size_t smem = TILE * sizeof(int) + (size_t)TILE_PAD * b.maxM * (POL == P_F64 ? sizeof(double) : sizeof(float4));
+    cudaError_t e = cudaSuccess;
+    auto fn = k_project_batch<POL, Q, CH, NBG>;
+    if (!smem_configured((const void*)fn, (int)smem)) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, nsm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, CTA, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(b.counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    int grid = std::max(1, std::min(per_sm * nsm, b.nitems));
+    fn<<<grid, CTA, smem, st>>>(b.views, b.args, b.items, b.nitems, b.counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project_batch(const BatchLaunch& b, dftu_prec prec, dftu_f64_mode mode, int variant, cudaStream_t st) {
+    cudaError_t e;
+    if (prec == DFTU_C64) {
+        switch (variant) {
+            case 1: e = run_project_batch<P_F32, 8, 8, 4>(b, st); break;
+            case 2: e = run_project_batch<P_F32, 16, 8, 4>(b, st); break;
+            case 3: e = run_project_batch<P_F32, 4, 16, 4>(b, st); break;
+            default: e = run_project_batch<P_F32, 8, 16, 4>(b, st); break;
+        }
+    } else if (mode == DFTU_F64_NATIVE) {
+        e = run_project_batch<P_F64, 8, 1, 4>(b, st);
+    } else {
+        switch (variant) {
+            case 1: e = run_project_batch<P_PAIR, 8, 4, 4>(b, st); break;
+            case 2: e = run_project_batch<P_PAIR, 4, 8, 4>(b, st); break;
+            case 3: e = run_project_batch<P_PAIR, 8, 8, 1>(b, st); break;
+            default: e = run_project_batch<P_PAIR, 8, 8, 4>(b, st); break;
+        }
+    }
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((b.max_reduce + 255) / 256), b.nsys);
+    k_tile_reduce_batch<<<grid, 256, 0, st>>>(b.views, b.args);
     return cudaGetLastError();
 }
 

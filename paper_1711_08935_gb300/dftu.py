@@ -31,7 +31,9 @@ EXPORTED = ["dftu_create", "dftu_setup_atoms", "dftu_get_sphere", "dftu_coulomb_
             "dftu_get_results", "dftu_get_renormalized", "dftu_get_projections", "dftu_total_orbitals",
             "dftu_atom_points", "dftu_sync_status", "dftu_last_error", "dftu_destroy",
             "dftu_set_kernel_variant", "dftu_kernel_variants", "dftu_project_sphere_noalloc",
-            "dftu_taylor_step"]
+            "dftu_taylor_step", "dftu_batch_create", "dftu_batch_bind", "dftu_batch_project",
+            "dftu_batch_occupations", "dftu_batch_acbn0_uj", "dftu_batch_apply", "dftu_batch_last_error",
+            "dftu_batch_destroy"]
 
 
 class DftuGrid(C.Structure):
@@ -77,6 +79,14 @@ def load() -> C.CDLL:
         "dftu_acbn0_uj": [vp, vp],
         "dftu_apply": [vp, vp, i32, i32, i64, vp, i32, vp],
         "dftu_taylor_step": [vp, vp, vp, i32, i32, i64, vp, d, i32, vp],
+        "dftu_batch_create": [C.POINTER(vp), i32, C.POINTER(vp)],
+        "dftu_batch_bind": [vp, C.POINTER(vp), i32, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(vp)],
+        "dftu_batch_project": [vp, vp],
+        "dftu_batch_occupations": [vp, vp],
+        "dftu_batch_acbn0_uj": [vp, vp],
+        "dftu_batch_apply": [vp, vp, i32, vp],
+        "dftu_batch_last_error": [vp],
+        "dftu_batch_destroy": [vp],
         "dftu_get_results": [vp, dp, dp, dp, dp, dp, vp],
         "dftu_get_renormalized": [vp, dp, dp, vp],
         "dftu_get_projections": [vp, dp, vp],
@@ -95,6 +105,8 @@ def load() -> C.CDLL:
         fn.restype = C.c_int
     L.dftu_last_error.restype = C.c_char_p
     L.dftu_destroy.restype = None
+    L.dftu_batch_last_error.restype = C.c_char_p
+    L.dftu_batch_destroy.restype = None
     _lib = L
     return L
 
@@ -299,6 +311,67 @@ class Handle:
 
     def sync_status(self) -> int:
         return self.lib.dftu_sync_status(self.h)
+
+
+class Batch:
+    """Many set-up handles processed by persistent launches (dftu_batch_*).  Keeps references to the
+    member handles and the bound tensors so they outlive the batch."""
+
+    def __init__(self, handles: Sequence[Handle]):
+        self.lib = load()
+        self.handles = list(handles)
+        arr = (C.c_void_p * len(handles))(*[h.h.value for h in handles])
+        b = C.c_void_p()
+        st = self.lib.dftu_batch_create(C.byref(b), len(handles), arr)
+        if st != DFTU_OK:
+            raise DftuError(st, "batch_create")
+        self.b = b
+        self.device = handles[0].device
+
+    def _check(self, st):
+        if st != DFTU_OK:
+            raise DftuError(st, self.lib.dftu_batch_last_error(self.b).decode())
+
+    def bind(self, psis: Sequence[torch.Tensor], fs: Sequence[torch.Tensor]):
+        n = len(self.handles)
+        prec = C128 if psis[0].dtype == torch.complex128 else C64
+        nb, ld = [], []
+        for h, p, f in zip(self.handles, psis, fs):
+            pr, nbi, ldi = h._psi_args(p)
+            if pr != prec:
+                raise ValueError("one precision for the whole batch")
+            if f.dtype != torch.float64 or not f.is_cuda or not f.is_contiguous():
+                raise ValueError("f must be contiguous float64 CUDA tensors")
+            nb.append(nbi)
+            ld.append(ldi)
+        self._keep = (list(psis), list(fs))
+        pa = (C.c_void_p * n)(*[p.data_ptr() for p in psis])
+        fa = (C.c_void_p * n)(*[f.data_ptr() for f in fs])
+        self._check(self.lib.dftu_batch_bind(self.b, pa, prec, (C.c_int * n)(*nb), (C.c_int64 * n)(*ld), fa))
+
+    def project(self, stream=None):
+        self._check(self.lib.dftu_batch_project(self.b, _stream_ptr(stream, self.device)))
+
+    def occupations(self, stream=None):
+        self._check(self.lib.dftu_batch_occupations(self.b, _stream_ptr(stream, self.device)))
+
+    def acbn0_uj(self, stream=None):
+        self._check(self.lib.dftu_batch_acbn0_uj(self.b, _stream_ptr(stream, self.device)))
+
+    def apply(self, coef: Optional[torch.Tensor] = None, accumulate: bool = True, stream=None):
+        cp = C.c_void_p(coef.data_ptr()) if coef is not None else None
+        self._check(self.lib.dftu_batch_apply(self.b, cp, 1 if accumulate else 0, _stream_ptr(stream, self.device)))
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.dftu_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def handle_for_system(system, max_bands: int, device: int = 0) -> Handle:

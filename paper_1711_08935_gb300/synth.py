@@ -306,3 +306,32 @@ def afm_spin_bias(system: System, strong: float = 0.85) -> List[float]:
         else:
             out.append(0.5)
     return out
+
+
+def molecule_systems(nsys: int, seed: int = 5, edge=(48, 80), natoms=(1, 8), radius=(4.0, 5.0), nstates=(20, 200),
+                     h: float = 0.3) -> List[System]:
+    """Independent isolated molecules: cubic boxes with edge drawn uniformly from `edge` (points) at
+    spacing h, 1-8 transition-metal d shells (hydrogenic 3d, Z_eff = 4) with radii uniform in `radius`
+    and centres uniform in the box shrunk by the radius, Gamma only, collinear spin.  The band count
+    of each system is drawn from `nstates` and stored in System.name as 'nb=<n>'."""
+    rng = np.random.default_rng(seed)
+    rad = hydrogenic_radial(3, 2, 4.0)
+    out = []
+    for s in range(nsys):
+        n = int(rng.integers(edge[0], edge[1] + 1))
+        g = Grid((n, n, n), (h, h, h), periodic=False)
+        L = n * h
+        na = int(rng.integers(natoms[0], natoms[1] + 1))
+        atoms = []
+        for _ in range(na):
+            R = float(rng.uniform(*radius))
+            lo, hi = R, max(R, L - R)
+            atoms.append(Atom(tuple(float(x) for x in rng.uniform(lo, hi, 3)), 0, 2, R))
+        nb = int(rng.integers(nstates[0], nstates[1] + 1))
+        out.append(System(g, atoms, [rad], np.zeros((1, 3)), np.ones(1), nspin=2, name=f"nb={nb}"))
+    return out
+
+
+def bands_of(system: System) -> int:
+    """Band count stored by molecule_systems."""
+    return int(system.name.split("nb=")[1])

@@ -1,0 +1,78 @@
+"""Batches of independent molecules (persistent launches over all members) against the same members
+run one by one through the single-system calls (bitwise: same arithmetic, same order), and one member
+against the CPU oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import dftu_oracle as O
+from paper_1711_08935_gb300 import dftu, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _members(dtype):
+    systems = synth.molecule_systems(5, seed=7, edge=(20, 28), natoms=(1, 3), radius=(2.0, 2.6), nstates=(3, 11))
+    dev = torch.device("cuda:0")
+    out = []
+    for i, s in enumerate(systems):
+        nb = synth.bands_of(s)
+        psi = synth.make_states(s, nb, seed=100 + i, device="cpu").to(dtype)
+        f = torch.from_numpy(synth.fermi_occupations(1, 2, nb, kT=0.05, e0=-0.2, de=0.04)).to(dev)
+        out.append((s, nb, psi, f))
+    return out
+
+
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+def test_batch_matches_single_system_calls_bitwise(dtype):
+    dev = torch.device("cuda:0")
+    mem = _members(dtype)
+    hs_a, hs_b, psis_a, psis_b, fs = [], [], [], [], []
+    for s, nb, psi, f in mem:
+        for hs, ps in ((hs_a, psis_a), (hs_b, psis_b)):
+            h = dftu.handle_for_system(s, nb)
+            h.coulomb_integrals(0)
+            hs.append(h)
+            ps.append(psi.to(dev).clone())
+        fs.append(f)
+    for h, p, f in zip(hs_a, psis_a, fs):                 # one by one
+        h.project(p); h.occupations(f); h.acbn0_uj(); h.apply(p)
+    batch = dftu.Batch(hs_b)
+    batch.bind(psis_b, fs)
+    batch.project(); batch.occupations(); batch.acbn0_uj(); batch.apply()
+    torch.cuda.synchronize()
+    for i, (ha, hb) in enumerate(zip(hs_a, hs_b)):
+        ra, rb = ha.results(), hb.results()
+        for na, nb_ in zip(ra["n"], rb["n"]):
+            assert np.array_equal(na, nb_), i
+        assert np.array_equal(ra["U"], rb["U"]) and np.array_equal(ra["J"], rb["J"]) and ra["EU"] == rb["EU"]
+        assert torch.equal(psis_a[i], psis_b[i]), i
+        assert hb.sync_status() in (dftu.DFTU_OK, dftu.DFTU_ERR_ZERO_DENOM)
+    batch.close()
+
+
+def test_batch_member_matches_oracle():
+    dev = torch.device("cuda:0")
+    mem = _members(torch.complex128)
+    hs, ps, fs = [], [], []
+    for s, nb, psi, f in mem:
+        h = dftu.handle_for_system(s, nb)
+        hs.append(h)
+        ps.append(psi.to(dev).clone())
+        fs.append(f)
+    s, nb, psi, f = mem[2]
+    st = O.setup_atoms(s)
+    coul = [O.coulomb_integrals(s.grid, s.atoms[0], st[0])]
+    for h in hs:
+        h.set_coulomb(0, coul[0])
+    batch = dftu.Batch(hs)
+    batch.bind(ps, fs)
+    batch.project(); batch.occupations(); batch.acbn0_uj(); batch.apply()
+    ref = O.hubbard_pass(s, st, psi.numpy(), f.cpu().numpy(), coulomb=coul)
+    r = hs[2].results()
+    for I in range(len(s.atoms)):
+        assert np.max(np.abs(r["n"][I] - O.paper_n(ref["occ"][I][0]))) < 1e-12
+    assert np.max(np.abs(r["U"] - ref["U"])) * O.HARTREE_EV < 1e-10
+    got = ps[2].cpu().numpy()
+    assert np.max(np.abs(got - ref["psi_out"])) < 1e-12 * np.max(np.abs(ref["psi_out"]))
+    batch.close()
