@@ -81,7 +81,7 @@ __device__ __forceinline__ double pair_to_double(float h, float l, int sc) {
 // Each lane handles U points of its band at a time: U loads in flight, then the arithmetic, then U
 // stores (the points of one tile are distinct grid points, so the batch never aliases).  Orbital rows
 // up to Q*U past the tile are staged as zeros, so the arithmetic needs no bounds test.
-template <int POL, int Q, int M, int U>
+template <int POL, int Q, int M, int U, int PF>
 __device__ __forceinline__ void apply_body(const Tile& t, const ApplyArgs& a, int64_t off, int q, int bl, const int* s_idx,
                                            const unsigned char* s_first, const unsigned char* after_idx,
                                            const unsigned char* after_c, int pe) {
@@ -99,6 +99,13 @@ __device__ __forceinline__ void apply_body(const Tile& t, const ApplyArgs& a, in
                 int i = i0 + u * Q;
                 x[u] = (i < t.np && (a.accumulate || !s_first[i])) ? row[s_idx[i]] : make_double2(0.0, 0.0);
             }
+            if (PF) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    int i = i0 + Q * U + u * Q;
+                    if (i < t.np) asm volatile("prefetch.global.L2 [%0];" ::"l"(row + s_idx[i]));
+                }
+            }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const double* ph = s_phi + (i0 + u * Q) * M;
@@ -115,9 +122,10 @@ __device__ __forceinline__ void apply_body(const Tile& t, const ApplyArgs& a, in
             }
         }
     } else if (POL == A_PAIR) {
-        // delta = sum_m phi_m c_m with the offset accumulator (C >= 4 sum|phi c|, residuals caught in a
-        // second float), then psi + delta as FP32 pairs at a common scale 2^(Em-1023), and the rounded
-        // double assembled with integer operations: no FP64 instruction on this path.
+        // delta = sum_m phi_m c_m with the offset accumulator (C >= 4 sum|phi c|: every partial sum stays in
+        // C's binade, so acc - s is exact and the rounding residual is caught in a second float), then the
+        // pair is renormalised, assembled into the nearest double with integer operations, and added to psi
+        // with one FP64 addition per component.
         double2* row = reinterpret_cast<double2*>(a.psi) + off;
         const float4* s_phi = reinterpret_cast<const float4*>(after_c);
         const float4* s_c = reinterpret_cast<const float4*>(after_idx);
@@ -135,13 +143,19 @@ __device__ __forceinline__ void apply_body(const Tile& t, const ApplyArgs& a, in
         const int ebound = min(max(pe + ce, -120), 120);          // |phi_hi c_hi| < 2^ebound
         const float Cv = pow2f(ebound + 5);
         const float2 C2 = make_float2(Cv, Cv), mone = make_float2(-1.f, -1.f);
-        const int Ed = ebound + 3 + 1023;                           // |delta| < 2^(Ed-1023)
         for (int i0 = q; i0 < t.np; i0 += Q * U) {
             double2 x[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 int i = i0 + u * Q;
                 x[u] = (i < t.np && (a.accumulate || !s_first[i])) ? row[s_idx[i]] : make_double2(0.0, 0.0);
+            }
+            if (PF) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    int i = i0 + Q * U + u * Q;
+                    if (i < t.np) asm volatile("prefetch.global.L2 [%0];" ::"l"(row + s_idx[i]));
+                }
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -160,24 +174,10 @@ __device__ __forceinline__ void apply_body(const Tile& t, const ApplyArgs& a, in
                     acc = sacc;
                 }
                 float2 dh = __fadd2_rn(acc, make_float2(-Cv, -Cv));          // exact
-                int Em = max(max(exp_field_d(x[u].x), exp_field_d(x[u].y)), Ed);
-                float2 xh, xl;
-                split_scaled_d(x[u].x, Em, xh.x, xl.x);
-                split_scaled_d(x[u].y, Em, xh.y, xl.y);
-                int k = 1023 - Em, k1 = k / 2;
-                float2 s1 = make_float2(pow2f(k1), pow2f(k1)), s2 = make_float2(pow2f(k - k1), pow2f(k - k1));
-                dh = __fmul2_rn(__fmul2_rn(dh, s1), s2);
-                float2 dl = __fmul2_rn(__fmul2_rn(lo, s1), s2);
-                // TwoSum(xh, dh), then the low parts, then renormalise (Fast2Sum)
-                float2 sum = __fadd2_rn(xh, dh);
-                float2 bb = __fadd2_rn(sum, make_float2(-xh.x, -xh.y));
-                float2 e = __fadd2_rn(__fadd2_rn(xh, make_float2(-(sum.x - bb.x), -(sum.y - bb.y))),
-                                      __fadd2_rn(dh, make_float2(-bb.x, -bb.y)));
-                e = __fadd2_rn(e, __fadd2_rn(xl, dl));
-                float2 hh = __fadd2_rn(sum, e);
-                float2 ll = __fadd2_rn(e, make_float2(-(hh.x - sum.x), -(hh.y - sum.y)));
-                x[u].x = pair_to_double(hh.x, ll.x, Em - 1023);
-                x[u].y = pair_to_double(hh.y, ll.y, Em - 1023);
+                float2 hh = __fadd2_rn(dh, lo);                               // Fast2Sum: |lo| << |dh| or dh = 0
+                float2 ll = __fadd2_rn(lo, make_float2(-(hh.x - dh.x), -(hh.y - dh.y)));
+                x[u].x += pair_to_double(hh.x, ll.x, 0);
+                x[u].y += pair_to_double(hh.y, ll.y, 0);
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -199,6 +199,13 @@ __device__ __forceinline__ void apply_body(const Tile& t, const ApplyArgs& a, in
                 int i = i0 + u * Q;
                 x[u] = (i < t.np && (a.accumulate || !s_first[i])) ? row[s_idx[i]] : make_float2(0.f, 0.f);
             }
+            if (PF) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    int i = i0 + Q * U + u * Q;
+                    if (i < t.np) asm volatile("prefetch.global.L2 [%0];" ::"l"(row + s_idx[i]));
+                }
+            }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const float4* ph = s_phi + (i0 + u * Q) * M;
@@ -218,7 +225,7 @@ __device__ __forceinline__ void apply_body(const Tile& t, const ApplyArgs& a, in
 }
 
 // One work item: tile `tile_id` (a tile of the current colour) of the system (v, a), component ks, band chunk `chunk`.
-template <int POL, int Q, int NBG, int U>
+template <int POL, int Q, int NBG, int U, int PF>
 __device__ __forceinline__ void apply_item(const View& v, const ApplyArgs& a, int tile_id, int ks, int chunk,
                                            unsigned char* smem, int& s_pe, unsigned char* s_first) {
     static_assert(Q * U <= TILE_PAD - TILE, "batched loops read up to Q*U rows past the tile");
@@ -307,25 +314,25 @@ __device__ __forceinline__ void apply_item(const View& v, const ApplyArgs& a, in
             const int64_t off = (int64_t)k * a.sk + (int64_t)s * a.ss + (int64_t)band * a.sn;
             const int pe = s_pe;
             switch (M) {
-                case 1: apply_body<POL, Q, 1, U>(t, a, off, q, bl, s_idx, s_first, after_idx, after_c, pe); break;
-                case 3: apply_body<POL, Q, 3, U>(t, a, off, q, bl, s_idx, s_first, after_idx, after_c, pe); break;
-                case 5: apply_body<POL, Q, 5, U>(t, a, off, q, bl, s_idx, s_first, after_idx, after_c, pe); break;
-                default: apply_body<POL, Q, 7, U>(t, a, off, q, bl, s_idx, s_first, after_idx, after_c, pe); break;
+                case 1: apply_body<POL, Q, 1, U, PF>(t, a, off, q, bl, s_idx, s_first, after_idx, after_c, pe); break;
+                case 3: apply_body<POL, Q, 3, U, PF>(t, a, off, q, bl, s_idx, s_first, after_idx, after_c, pe); break;
+                case 5: apply_body<POL, Q, 5, U, PF>(t, a, off, q, bl, s_idx, s_first, after_idx, after_c, pe); break;
+                default: apply_body<POL, Q, 7, U, PF>(t, a, off, q, bl, s_idx, s_first, after_idx, after_c, pe); break;
             }
         }
     }
 }
 
-template <int POL, int Q, int NBG, int U>
+template <int POL, int Q, int NBG, int U, int PF>
 __global__ void __launch_bounds__(CTA, 3) k_apply(View v, ApplyArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_pe;
     __shared__ unsigned char s_first[TILE];
-    apply_item<POL, Q, NBG, U>(v, a, a.tile_list[blockIdx.x], blockIdx.z, blockIdx.y, smem, s_pe, s_first);
+    apply_item<POL, Q, NBG, U, PF>(v, a, a.tile_list[blockIdx.x], blockIdx.z, blockIdx.y, smem, s_pe, s_first);
 }
 
 // Persistent form over many systems: (system, tile, k*spin) items of one colour from a counter.
-template <int POL, int Q, int NBG, int U>
+template <int POL, int Q, int NBG, int U, int PF>
 __global__ void __launch_bounds__(CTA, 3) k_apply_batch(const View* __restrict__ views, const ProjArgs* __restrict__ args,
                                                         const int4* __restrict__ items, int nitems, int* counter,
                                                         const double* coef, int accumulate) {
@@ -344,27 +351,27 @@ __global__ void __launch_bounds__(CTA, 3) k_apply_batch(const View* __restrict__
         ApplyArgs a{const_cast<void*>(pa.psi), pa.sk, pa.ss, pa.sn, pa.nbands, coef, nullptr, accumulate};
         const int nchunks = (pa.nbands + BPC * NBG - 1) / (BPC * NBG);
         for (int c = 0; c < nchunks; ++c) {
-            apply_item<POL, Q, NBG, U>(v, a, w.y, w.z, c, smem, s_pe, s_first);
+            apply_item<POL, Q, NBG, U, PF>(v, a, w.y, w.z, c, smem, s_pe, s_first);
             __syncthreads();
         }
     }
 }
 
-template <int POL, int Q, int NBG, int U>
+template <int POL, int Q, int NBG, int U, int PF>
 static cudaError_t run_apply(const View& v, ApplyArgs a, const int* color_order, const std::vector<int>& color_beg,
                              cudaStream_t st) {
     constexpr int BPC = (CTA / 32) * (32 / Q);
     size_t smem = TILE * sizeof(int) + BPC * MAXM * 16 + (size_t)TILE_PAD * v.maxM * (POL == A_F64 ? sizeof(double) : sizeof(float4));
     cudaError_t e = cudaSuccess;
-    if (!smem_configured((const void*)k_apply<POL, Q, NBG, U>, (int)smem))
-        e = cudaFuncSetAttribute(k_apply<POL, Q, NBG, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (!smem_configured((const void*)k_apply<POL, Q, NBG, U, PF>, (int)smem))
+        e = cudaFuncSetAttribute(k_apply<POL, Q, NBG, U, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     for (size_t c = 0; c + 1 < color_beg.size(); ++c) {
         int n = color_beg[c + 1] - color_beg[c];
         if (n == 0) continue;
         a.tile_list = color_order + color_beg[c];
         dim3 grid(n, (a.nbands + BPC * NBG - 1) / (BPC * NBG), v.nk * v.ns);
-        k_apply<POL, Q, NBG, U><<<grid, CTA, smem, st>>>(v, a);
+        k_apply<POL, Q, NBG, U, PF><<<grid, CTA, smem, st>>>(v, a);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -377,18 +384,22 @@ cudaError_t launch_apply(const View& v, void* psi, dftu_prec prec, dftu_f64_mode
     ApplyArgs a{psi, sk, ss, sn, nbands, coef, nullptr, accumulate};
     if (prec == DFTU_C64) {
         switch (variant) {   // (lanes per band, band groups per CTA, points in flight per lane)
-            case 1: return run_apply<A_F32, 8, 4, 4>(v, a, color_order, color_beg, st);
-            case 2: return run_apply<A_F32, 4, 4, 8>(v, a, color_order, color_beg, st);
-            case 3: return run_apply<A_F32, 16, 4, 4>(v, a, color_order, color_beg, st);
-            default: return run_apply<A_F32, 8, 4, 8>(v, a, color_order, color_beg, st);
+            case 1: return run_apply<A_F32, 8, 4, 4, 0>(v, a, color_order, color_beg, st);
+            case 2: return run_apply<A_F32, 4, 4, 8, 0>(v, a, color_order, color_beg, st);
+            case 3: return run_apply<A_F32, 16, 4, 4, 0>(v, a, color_order, color_beg, st);
+            case 4: return run_apply<A_F32, 8, 4, 8, 1>(v, a, color_order, color_beg, st);
+            case 5: return run_apply<A_F32, 8, 4, 4, 1>(v, a, color_order, color_beg, st);
+            default: return run_apply<A_F32, 8, 4, 8, 0>(v, a, color_order, color_beg, st);
         }
     }
-    if (mode == DFTU_F64_NATIVE) return run_apply<A_F64, 8, 4, 4>(v, a, color_order, color_beg, st);
+    if (mode == DFTU_F64_NATIVE) return run_apply<A_F64, 8, 4, 4, 0>(v, a, color_order, color_beg, st);
     switch (variant) {
-        case 1: return run_apply<A_PAIR, 8, 4, 2>(v, a, color_order, color_beg, st);
-        case 2: return run_apply<A_PAIR, 4, 4, 4>(v, a, color_order, color_beg, st);
-        case 3: return run_apply<A_PAIR, 8, 4, 8>(v, a, color_order, color_beg, st);
-        default: return run_apply<A_PAIR, 8, 4, 4>(v, a, color_order, color_beg, st);
+        case 1: return run_apply<A_PAIR, 8, 4, 2, 0>(v, a, color_order, color_beg, st);
+        case 2: return run_apply<A_PAIR, 4, 4, 4, 0>(v, a, color_order, color_beg, st);
+        case 3: return run_apply<A_PAIR, 8, 4, 8, 0>(v, a, color_order, color_beg, st);
+        case 4: return run_apply<A_PAIR, 8, 4, 4, 1>(v, a, color_order, color_beg, st);
+        case 5: return run_apply<A_PAIR, 4, 4, 4, 1>(v, a, color_order, color_beg, st);
+        default: return run_apply<A_PAIR, 8, 4, 4, 0>(v, a, color_order, color_beg, st);
     }
 }
 
@@ -403,11 +414,11 @@ cudaError_t launch_taylor_coefs(double dt, int order, double* coefs, cudaStream_
     return cudaGetLastError();
 }
 
-template <int POL, int Q, int NBG, int U>
+template <int POL, int Q, int NBG, int U, int PF>
 static cudaError_t run_apply_batch(const BatchLaunch& b, const double* coef, int accumulate, cudaStream_t st) {
     constexpr int BPC = (CTA / 32) * (32 / Q);
     size_t smem = TILE * sizeof(int) + BPC * MAXM * 16 + (size_t)TILE_PAD * b.maxM * (POL == A_F64 ? sizeof(double) : sizeof(float4));
-    auto fn = k_apply_batch<POL, Q, NBG, U>;
+    auto fn = k_apply_batch<POL, Q, NBG, U, PF>;
     cudaError_t e = cudaSuccess;
     if (!smem_configured((const void*)fn, (int)smem)) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -433,18 +444,22 @@ cudaError_t launch_apply_batch(const BatchLaunch& b, dftu_prec prec, dftu_f64_mo
                                int accumulate, cudaStream_t st) {
     if (prec == DFTU_C64) {
         switch (variant) {
-            case 1: return run_apply_batch<A_F32, 8, 4, 4>(b, coef, accumulate, st);
-            case 2: return run_apply_batch<A_F32, 4, 4, 8>(b, coef, accumulate, st);
-            case 3: return run_apply_batch<A_F32, 16, 4, 4>(b, coef, accumulate, st);
-            default: return run_apply_batch<A_F32, 8, 4, 8>(b, coef, accumulate, st);
+            case 1: return run_apply_batch<A_F32, 8, 4, 4, 0>(b, coef, accumulate, st);
+            case 2: return run_apply_batch<A_F32, 4, 4, 8, 0>(b, coef, accumulate, st);
+            case 3: return run_apply_batch<A_F32, 16, 4, 4, 0>(b, coef, accumulate, st);
+            case 4: return run_apply_batch<A_F32, 8, 4, 8, 1>(b, coef, accumulate, st);
+            case 5: return run_apply_batch<A_F32, 8, 4, 4, 1>(b, coef, accumulate, st);
+            default: return run_apply_batch<A_F32, 8, 4, 8, 0>(b, coef, accumulate, st);
         }
     }
-    if (mode == DFTU_F64_NATIVE) return run_apply_batch<A_F64, 8, 4, 4>(b, coef, accumulate, st);
+    if (mode == DFTU_F64_NATIVE) return run_apply_batch<A_F64, 8, 4, 4, 0>(b, coef, accumulate, st);
     switch (variant) {
-        case 1: return run_apply_batch<A_PAIR, 8, 4, 2>(b, coef, accumulate, st);
-        case 2: return run_apply_batch<A_PAIR, 4, 4, 4>(b, coef, accumulate, st);
-        case 3: return run_apply_batch<A_PAIR, 8, 4, 8>(b, coef, accumulate, st);
-        default: return run_apply_batch<A_PAIR, 8, 4, 4>(b, coef, accumulate, st);
+        case 1: return run_apply_batch<A_PAIR, 8, 4, 2, 0>(b, coef, accumulate, st);
+        case 2: return run_apply_batch<A_PAIR, 4, 4, 4, 0>(b, coef, accumulate, st);
+        case 3: return run_apply_batch<A_PAIR, 8, 4, 8, 0>(b, coef, accumulate, st);
+        case 4: return run_apply_batch<A_PAIR, 8, 4, 4, 1>(b, coef, accumulate, st);
+        case 5: return run_apply_batch<A_PAIR, 4, 4, 4, 1>(b, coef, accumulate, st);
+        default: return run_apply_batch<A_PAIR, 8, 4, 4, 0>(b, coef, accumulate, st);
     }
 }
 

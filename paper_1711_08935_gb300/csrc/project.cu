@@ -31,7 +31,10 @@ namespace dftu {
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
-struct DF2 { float2 h, l; };   // (re, im) pair of double-float numbers
+struct DF2 { float2 h, l; };
+
+// Ask L2 to start fetching a line a later chain will read (no register is held for it).
+__device__ __forceinline__ void prefetch_l2(const void* ptr) { asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr)); }   // (re, im) pair of double-float numbers
 
 // TwoSum(a.h, b.h) with the low parts added: a <- a + b.
 __device__ __forceinline__ void df_add(DF2& a, const DF2& b) {
@@ -109,7 +112,7 @@ __device__ __forceinline__ void proj_body_f64(const View& v, const Tile& t, int 
 // ------------------------------------------------------------------------------------------------
 // F32 policy (complex64 states)
 // ------------------------------------------------------------------------------------------------
-template <int M, int Q, int CH>
+template <int M, int Q, int CH, int PF>
 __device__ __forceinline__ void proj_body_f32(const View& v, const Tile& t, int ks, int band, const float2* __restrict__ row,
                                               const int* s_idx, const float4* s_phi) {
     const int q = threadIdx.x & (Q - 1);
@@ -123,6 +126,13 @@ __device__ __forceinline__ void proj_body_f32(const View& v, const Tile& t, int 
             for (int c = 0; c < CH; ++c) {
                 int i = i0 + c * Q;
                 x[c] = (i < t.np) ? __ldg(row + s_idx[i]) : make_float2(0.f, 0.f);
+            }
+            if (PF) {
+#pragma unroll
+                for (int c = 0; c < CH; ++c) {
+                    int i = i0 + Q * CH + c * Q;
+                    if (i < t.np) prefetch_l2(row + s_idx[i]);
+                }
             }
             DF2 ch[M];
 #pragma unroll
@@ -177,7 +187,7 @@ __device__ __forceinline__ void split_scaled(double x, int Em, float& hi, float&
 
 __device__ __forceinline__ int exp_field(double x) { return (__double2hiint(x) >> 20) & 0x7FF; }
 
-template <int M, int Q, int CH>
+template <int M, int Q, int CH, int PF>
 __device__ __forceinline__ void proj_body_pair(const View& v, const Tile& t, int ks, int band, const double2* __restrict__ row,
                                                const int* s_idx, const float4* s_phi, int pe) {
     const int q = threadIdx.x & (Q - 1);
@@ -198,6 +208,13 @@ __device__ __forceinline__ void proj_body_pair(const View& v, const Tile& t, int
             for (int c = 0; c < CH; ++c) {
                 int i = i0 + c * Q;
                 x[c] = (i < t.np) ? __ldg(row + s_idx[i]) : make_double2(0.0, 0.0);
+            }
+            if (PF) {
+#pragma unroll
+                for (int c = 0; c < CH; ++c) {
+                    int i = i0 + Q * CH + c * Q;
+                    if (i < t.np) prefetch_l2(row + s_idx[i]);
+                }
             }
             int Ec = 0;
 #pragma unroll
@@ -285,7 +302,7 @@ enum Pol { P_F64 = 0, P_PAIR = 1, P_F32 = 2 };
 
 // One work item: tile `tile_id` of the system described by (v, a), spin/component index ks, every band of
 // band chunk `chunk` (NBG groups of BPC bands).  The tile is staged in shared memory once.
-template <int POL, int Q, int CH, int NBG>
+template <int POL, int Q, int CH, int NBG, int PF>
 __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, int tile_id, int ks, int chunk,
                                              unsigned char* smem, int* s_pe) {
     int* s_idx = reinterpret_cast<int*>(smem);
@@ -336,34 +353,34 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
             const double2* row = active ? reinterpret_cast<const double2*>(a.psi) + off : nullptr;
             const int pe = *s_pe;
             switch (t.M) {
-                case 1: proj_body_pair<1, Q, CH>(v, t, ks, band, row, s_idx, s_phi, pe); break;
-                case 3: proj_body_pair<3, Q, CH>(v, t, ks, band, row, s_idx, s_phi, pe); break;
-                case 5: proj_body_pair<5, Q, CH>(v, t, ks, band, row, s_idx, s_phi, pe); break;
-                default: proj_body_pair<7, Q, CH>(v, t, ks, band, row, s_idx, s_phi, pe); break;
+                case 1: proj_body_pair<1, Q, CH, PF>(v, t, ks, band, row, s_idx, s_phi, pe); break;
+                case 3: proj_body_pair<3, Q, CH, PF>(v, t, ks, band, row, s_idx, s_phi, pe); break;
+                case 5: proj_body_pair<5, Q, CH, PF>(v, t, ks, band, row, s_idx, s_phi, pe); break;
+                default: proj_body_pair<7, Q, CH, PF>(v, t, ks, band, row, s_idx, s_phi, pe); break;
             }
         } else {
             const float4* s_phi = reinterpret_cast<const float4*>(smem + TILE * sizeof(int));
             const float2* row = active ? reinterpret_cast<const float2*>(a.psi) + off : nullptr;
             switch (t.M) {
-                case 1: proj_body_f32<1, Q, CH>(v, t, ks, band, row, s_idx, s_phi); break;
-                case 3: proj_body_f32<3, Q, CH>(v, t, ks, band, row, s_idx, s_phi); break;
-                case 5: proj_body_f32<5, Q, CH>(v, t, ks, band, row, s_idx, s_phi); break;
-                default: proj_body_f32<7, Q, CH>(v, t, ks, band, row, s_idx, s_phi); break;
+                case 1: proj_body_f32<1, Q, CH, PF>(v, t, ks, band, row, s_idx, s_phi); break;
+                case 3: proj_body_f32<3, Q, CH, PF>(v, t, ks, band, row, s_idx, s_phi); break;
+                case 5: proj_body_f32<5, Q, CH, PF>(v, t, ks, band, row, s_idx, s_phi); break;
+                default: proj_body_f32<7, Q, CH, PF>(v, t, ks, band, row, s_idx, s_phi); break;
             }
         }
     }
 }
 
-template <int POL, int Q, int CH, int NBG>
+template <int POL, int Q, int CH, int NBG, int PF>
 __global__ void __launch_bounds__(CTA, 2) k_project(View v, ProjArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_pe;
-    project_item<POL, Q, CH, NBG>(v, a, blockIdx.x, blockIdx.z, blockIdx.y, smem, &s_pe);
+    project_item<POL, Q, CH, NBG, PF>(v, a, blockIdx.x, blockIdx.z, blockIdx.y, smem, &s_pe);
 }
 
 // Persistent form over many systems: every CTA takes (system, tile, k*spin) items from a counter until
 // the list is exhausted and processes all band chunks of the item's system.
-template <int POL, int Q, int CH, int NBG>
+template <int POL, int Q, int CH, int NBG, int PF>
 __global__ void __launch_bounds__(CTA, 2) k_project_batch(const View* __restrict__ views, const ProjArgs* __restrict__ args,
                                                           const int4* __restrict__ items, int nitems, int* counter) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -379,7 +396,7 @@ __global__ void __launch_bounds__(CTA, 2) k_project_batch(const View* __restrict
         const ProjArgs& a = args[w.x];
         const int nchunks = (a.nbands + BPC * NBG - 1) / (BPC * NBG);
         for (int c = 0; c < nchunks; ++c) {
-            project_item<POL, Q, CH, NBG>(v, a, w.y, w.z, c, smem, &s_pe);
+            project_item<POL, Q, CH, NBG, PF>(v, a, w.y, w.z, c, smem, &s_pe);
             __syncthreads();   // the next chunk or item restages shared memory
         }
     }
@@ -431,17 +448,17 @@ __global__ void k_tile_reduce_batch(const View* __restrict__ views, const ProjAr
     tile_reduce_elem(views[blockIdx.y], args[blockIdx.y].nbands, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-template <int POL, int Q, int CH, int NBG>
+template <int POL, int Q, int CH, int NBG, int PF>
 static cudaError_t run_project(const View& v, const ProjArgs& a, cudaStream_t st) {
     static_assert(Q * CH <= TILE_PAD - TILE, "chained loops read up to Q*CH rows past the tile");
     size_t smem = TILE * sizeof(int) + (size_t)TILE_PAD * v.maxM * (POL == P_F64 ? sizeof(double) : sizeof(float4));
     cudaError_t e = cudaSuccess;
-    if (!smem_configured((const void*)k_project<POL, Q, CH, NBG>, (int)smem))
-        e = cudaFuncSetAttribute(k_project<POL, Q, CH, NBG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (!smem_configured((const void*)k_project<POL, Q, CH, NBG, PF>, (int)smem))
+        e = cudaFuncSetAttribute(k_project<POL, Q, CH, NBG, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     constexpr int BPC = (CTA / 32) * (32 / Q);
     dim3 grid(v.ntiles, (a.nbands + BPC * NBG - 1) / (BPC * NBG), v.nk * v.ns);
-    k_project<POL, Q, CH, NBG><<<grid, CTA, smem, st>>>(v, a);
+    k_project<POL, Q, CH, NBG, PF><<<grid, CTA, smem, st>>>(v, a);
     return cudaGetLastError();
 }
 
@@ -451,19 +468,23 @@ cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_
     cudaError_t e;
     if (prec == DFTU_C64) {
         switch (variant) {   // (lanes per band, points per chain, band groups per CTA)
-            case 1: e = run_project<P_F32, 8, 8, 4>(v, a, st); break;
-            case 2: e = run_project<P_F32, 16, 8, 4>(v, a, st); break;
-            case 3: e = run_project<P_F32, 4, 16, 4>(v, a, st); break;
-            default: e = run_project<P_F32, 8, 16, 4>(v, a, st); break;
+            case 1: e = run_project<P_F32, 8, 8, 4, 0>(v, a, st); break;
+            case 2: e = run_project<P_F32, 16, 8, 4, 0>(v, a, st); break;
+            case 3: e = run_project<P_F32, 4, 16, 4, 0>(v, a, st); break;
+            case 4: e = run_project<P_F32, 8, 16, 4, 1>(v, a, st); break;
+            case 5: e = run_project<P_F32, 4, 16, 4, 1>(v, a, st); break;
+            default: e = run_project<P_F32, 8, 16, 4, 0>(v, a, st); break;
         }
     } else if (mode == DFTU_F64_NATIVE) {
-        e = run_project<P_F64, 8, 1, 4>(v, a, st);
+        e = run_project<P_F64, 8, 1, 4, 0>(v, a, st);
     } else {
         switch (variant) {
-            case 1: e = run_project<P_PAIR, 8, 4, 4>(v, a, st); break;
-            case 2: e = run_project<P_PAIR, 4, 8, 4>(v, a, st); break;
-            case 3: e = run_project<P_PAIR, 8, 8, 1>(v, a, st); break;
-            default: e = run_project<P_PAIR, 8, 8, 4>(v, a, st); break;
+            case 1: e = run_project<P_PAIR, 8, 4, 4, 0>(v, a, st); break;
+            case 2: e = run_project<P_PAIR, 4, 8, 4, 0>(v, a, st); break;
+            case 3: e = run_project<P_PAIR, 8, 8, 1, 0>(v, a, st); break;
+            case 4: e = run_project<P_PAIR, 4, 8, 4, 1>(v, a, st); break;
+            case 5: e = run_project<P_PAIR, 8, 8, 4, 1>(v, a, st); break;
+            default: e = run_project<P_PAIR, 8, 8, 4, 0>(v, a, st); break;
         }
     }
     if (e != cudaSuccess) return e;
@@ -472,11 +493,11 @@ cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_
     return cudaGetLastError();
 }
 
-template <int POL, int Q, int CH, int NBG>
+template <int POL, int Q, int CH, int NBG, int PF>
 static cudaError_t run_project_batch(const BatchLaunch& b, cudaStream_t st) {
     size_t smem = TILE * sizeof(int) + (size_t)TILE_PAD * b.maxM * (POL == P_F64 ? sizeof(double) : sizeof(float4));
     cudaError_t e = cudaSuccess;
-    auto fn = k_project_batch<POL, Q, CH, NBG>;
+    auto fn = k_project_batch<POL, Q, CH, NBG, PF>;
     if (!smem_configured((const void*)fn, (int)smem)) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0, nsm = 0, dev = 0;
@@ -495,19 +516,23 @@ cudaError_t launch_project_batch(const BatchLaunch& b, dftu_prec prec, dftu_f64_
     cudaError_t e;
     if (prec == DFTU_C64) {
         switch (variant) {
-            case 1: e = run_project_batch<P_F32, 8, 8, 4>(b, st); break;
-            case 2: e = run_project_batch<P_F32, 16, 8, 4>(b, st); break;
-            case 3: e = run_project_batch<P_F32, 4, 16, 4>(b, st); break;
-            default: e = run_project_batch<P_F32, 8, 16, 4>(b, st); break;
+            case 1: e = run_project_batch<P_F32, 8, 8, 4, 0>(b, st); break;
+            case 2: e = run_project_batch<P_F32, 16, 8, 4, 0>(b, st); break;
+            case 3: e = run_project_batch<P_F32, 4, 16, 4, 0>(b, st); break;
+            case 4: e = run_project_batch<P_F32, 8, 16, 4, 1>(b, st); break;
+            case 5: e = run_project_batch<P_F32, 4, 16, 4, 1>(b, st); break;
+            default: e = run_project_batch<P_F32, 8, 16, 4, 0>(b, st); break;
         }
     } else if (mode == DFTU_F64_NATIVE) {
-        e = run_project_batch<P_F64, 8, 1, 4>(b, st);
+        e = run_project_batch<P_F64, 8, 1, 4, 0>(b, st);
     } else {
         switch (variant) {
-            case 1: e = run_project_batch<P_PAIR, 8, 4, 4>(b, st); break;
-            case 2: e = run_project_batch<P_PAIR, 4, 8, 4>(b, st); break;
-            case 3: e = run_project_batch<P_PAIR, 8, 8, 1>(b, st); break;
-            default: e = run_project_batch<P_PAIR, 8, 8, 4>(b, st); break;
+            case 1: e = run_project_batch<P_PAIR, 8, 4, 4, 0>(b, st); break;
+            case 2: e = run_project_batch<P_PAIR, 4, 8, 4, 0>(b, st); break;
+            case 3: e = run_project_batch<P_PAIR, 8, 8, 1, 0>(b, st); break;
+            case 4: e = run_project_batch<P_PAIR, 4, 8, 4, 1>(b, st); break;
+            case 5: e = run_project_batch<P_PAIR, 8, 8, 4, 1>(b, st); break;
+            default: e = run_project_batch<P_PAIR, 8, 8, 4, 0>(b, st); break;
         }
     }
     if (e != cudaSuccess) return e;
