@@ -157,7 +157,7 @@ cudaError_t launch_orbitals(const View& v, const double* radial_tab, const int* 
                             const int* radial_nr, const double* radial_dr, cudaStream_t st);
 cudaError_t launch_lowdin(const View& v, double* work_S, cudaStream_t st);
 
-constexpr int NVARIANTS = 6;   // shapes per streaming kernel (see dftu_set_kernel_variant)
+constexpr int NVARIANTS = 8;   // shapes per streaming kernel (see dftu_set_kernel_variant)
 cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_f64_mode mode, int nbands,
                            int64_t sk, int64_t ss, int64_t sn, int variant, cudaStream_t st);
 cudaError_t launch_nbar(const View& v, int nbands, cudaStream_t st);

@@ -371,8 +371,8 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
     }
 }
 
-template <int POL, int Q, int CH, int NBG, int PF>
-__global__ void __launch_bounds__(CTA, 2) k_project(View v, ProjArgs a) {
+template <int POL, int Q, int CH, int NBG, int PF, int MINB>
+__global__ void __launch_bounds__(CTA, MINB) k_project(View v, ProjArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_pe;
     project_item<POL, Q, CH, NBG, PF>(v, a, blockIdx.x, blockIdx.z, blockIdx.y, smem, &s_pe);
@@ -380,8 +380,8 @@ __global__ void __launch_bounds__(CTA, 2) k_project(View v, ProjArgs a) {
 
 // Persistent form over many systems: every CTA takes (system, tile, k*spin) items from a counter until
 // the list is exhausted and processes all band chunks of the item's system.
-template <int POL, int Q, int CH, int NBG, int PF>
-__global__ void __launch_bounds__(CTA, 2) k_project_batch(const View* __restrict__ views, const ProjArgs* __restrict__ args,
+template <int POL, int Q, int CH, int NBG, int PF, int MINB>
+__global__ void __launch_bounds__(CTA, MINB) k_project_batch(const View* __restrict__ views, const ProjArgs* __restrict__ args,
                                                           const int4* __restrict__ items, int nitems, int* counter) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_pe, s_item;
@@ -448,17 +448,17 @@ __global__ void k_tile_reduce_batch(const View* __restrict__ views, const ProjAr
     tile_reduce_elem(views[blockIdx.y], args[blockIdx.y].nbands, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-template <int POL, int Q, int CH, int NBG, int PF>
+template <int POL, int Q, int CH, int NBG, int PF, int MINB = 2>
 static cudaError_t run_project(const View& v, const ProjArgs& a, cudaStream_t st) {
     static_assert(Q * CH <= TILE_PAD - TILE, "chained loops read up to Q*CH rows past the tile");
     size_t smem = TILE * sizeof(int) + (size_t)TILE_PAD * v.maxM * (POL == P_F64 ? sizeof(double) : sizeof(float4));
     cudaError_t e = cudaSuccess;
-    if (!smem_configured((const void*)k_project<POL, Q, CH, NBG, PF>, (int)smem))
-        e = cudaFuncSetAttribute(k_project<POL, Q, CH, NBG, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (!smem_configured((const void*)k_project<POL, Q, CH, NBG, PF, MINB>, (int)smem))
+        e = cudaFuncSetAttribute(k_project<POL, Q, CH, NBG, PF, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     constexpr int BPC = (CTA / 32) * (32 / Q);
     dim3 grid(v.ntiles, (a.nbands + BPC * NBG - 1) / (BPC * NBG), v.nk * v.ns);
-    k_project<POL, Q, CH, NBG, PF><<<grid, CTA, smem, st>>>(v, a);
+    k_project<POL, Q, CH, NBG, PF, MINB><<<grid, CTA, smem, st>>>(v, a);
     return cudaGetLastError();
 }
 
@@ -473,6 +473,8 @@ cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_
             case 3: e = run_project<P_F32, 4, 16, 4, 0>(v, a, st); break;
             case 4: e = run_project<P_F32, 8, 16, 4, 1>(v, a, st); break;
             case 5: e = run_project<P_F32, 4, 16, 4, 1>(v, a, st); break;
+            case 6: e = run_project<P_F32, 8, 8, 4, 0, 3>(v, a, st); break;
+            case 7: e = run_project<P_F32, 4, 8, 4, 1, 4>(v, a, st); break;
             default: e = run_project<P_F32, 8, 16, 4, 0>(v, a, st); break;
         }
     } else if (mode == DFTU_F64_NATIVE) {
@@ -484,6 +486,8 @@ cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_
             case 3: e = run_project<P_PAIR, 8, 8, 1, 0>(v, a, st); break;
             case 4: e = run_project<P_PAIR, 4, 8, 4, 1>(v, a, st); break;
             case 5: e = run_project<P_PAIR, 8, 8, 4, 1>(v, a, st); break;
+            case 6: e = run_project<P_PAIR, 4, 4, 4, 0, 3>(v, a, st); break;
+            case 7: e = run_project<P_PAIR, 4, 8, 4, 1, 3>(v, a, st); break;
             default: e = run_project<P_PAIR, 8, 8, 4, 0>(v, a, st); break;
         }
     }
@@ -493,11 +497,11 @@ cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_
     return cudaGetLastError();
 }
 
-template <int POL, int Q, int CH, int NBG, int PF>
+template <int POL, int Q, int CH, int NBG, int PF, int MINB = 2>
 static cudaError_t run_project_batch(const BatchLaunch& b, cudaStream_t st) {
     size_t smem = TILE * sizeof(int) + (size_t)TILE_PAD * b.maxM * (POL == P_F64 ? sizeof(double) : sizeof(float4));
     cudaError_t e = cudaSuccess;
-    auto fn = k_project_batch<POL, Q, CH, NBG, PF>;
+    auto fn = k_project_batch<POL, Q, CH, NBG, PF, MINB>;
     if (!smem_configured((const void*)fn, (int)smem)) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0, nsm = 0, dev = 0;
@@ -521,6 +525,8 @@ cudaError_t launch_project_batch(const BatchLaunch& b, dftu_prec prec, dftu_f64_
             case 3: e = run_project_batch<P_F32, 4, 16, 4, 0>(b, st); break;
             case 4: e = run_project_batch<P_F32, 8, 16, 4, 1>(b, st); break;
             case 5: e = run_project_batch<P_F32, 4, 16, 4, 1>(b, st); break;
+            case 6: e = run_project_batch<P_F32, 8, 8, 4, 0, 3>(b, st); break;
+            case 7: e = run_project_batch<P_F32, 4, 8, 4, 1, 4>(b, st); break;
             default: e = run_project_batch<P_F32, 8, 16, 4, 0>(b, st); break;
         }
     } else if (mode == DFTU_F64_NATIVE) {
@@ -532,6 +538,8 @@ cudaError_t launch_project_batch(const BatchLaunch& b, dftu_prec prec, dftu_f64_
             case 3: e = run_project_batch<P_PAIR, 8, 8, 1, 0>(b, st); break;
             case 4: e = run_project_batch<P_PAIR, 4, 8, 4, 1>(b, st); break;
             case 5: e = run_project_batch<P_PAIR, 8, 8, 4, 1>(b, st); break;
+            case 6: e = run_project_batch<P_PAIR, 4, 4, 4, 0, 3>(b, st); break;
+            case 7: e = run_project_batch<P_PAIR, 4, 8, 4, 1, 3>(b, st); break;
             default: e = run_project_batch<P_PAIR, 8, 8, 4, 0>(b, st); break;
         }
     }
