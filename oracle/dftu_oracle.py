@@ -479,6 +479,31 @@ def taylor_step(system, atoms_setup, psi, f, dt, coulomb=None, fixed_u=None, ord
 
 
 # ------------------------------------------------------------------------------------------------
+# Hubbard forces (Sec. IV): F = -dE_U/dR with dn/dR from projections of the state gradients
+# ------------------------------------------------------------------------------------------------
+
+def hubbard_forces(system, atoms_setup, psi, dpsi, f, V_atoms):
+    """Sec. IV, in the form that differentiates the states instead of the orbitals:
+    dn_{ab}/dR_i = sum w f [<d_i psi|phi_a><phi_b|psi> + <psi|phi_a><phi_b|d_i psi>], and
+    F_i = -sum_{sigma,a,b} (dE_U/dn_{ab}) dn_{ab}/dR_i with dE_U/dn_{ab} = U_eff/2 (delta_ab - 2 n_ba),
+    which is V_ab of Eq. (6) under the transposition reading.  U_eff is held fixed, as in the paper.
+    Collinear/unpolarised psi[k][s][n][npts]; dpsi = [d_x psi, d_y psi, d_z psi]; V_atoms[I] is [s][M][M].
+    Returns [natoms][3] in Hartree/bohr."""
+    p = project(system, atoms_setup, psi)
+    pg = [project(system, atoms_setup, d) for d in dpsi]
+    wf = np.asarray(system.wk)[:, None, None] * f
+    mult = 2.0 if system.nspin == 1 else 1.0
+    F = np.zeros((len(atoms_setup), 3))
+    for I in range(len(atoms_setup)):
+        for i in range(3):
+            a, b = p[I], pg[i][I]                                   # [k][s][n][m]
+            dn = (np.einsum("ksn,ksnm,ksnq->smq", wf, np.conj(b), a)
+                  + np.einsum("ksn,ksnm,ksnq->smq", wf, np.conj(a), b))
+            F[I, i] = -mult * float(np.real(np.einsum("smq,smq->", V_atoms[I], dn)))
+    return F
+
+
+# ------------------------------------------------------------------------------------------------
 # Coulomb integrals (mm'|m''m''') on the real-space grid (Sec. III; definition Eq. B2)
 # ------------------------------------------------------------------------------------------------
 

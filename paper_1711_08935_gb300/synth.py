@@ -335,3 +335,43 @@ def molecule_systems(nsys: int, seed: int = 5, edge=(48, 80), natoms=(1, 8), rad
 def bands_of(system: System) -> int:
     """Band count stored by molecule_systems."""
     return int(system.name.split("nb=")[1])
+
+
+def analytic_states(system: System, nbands: int, seed: int, shift=(0.0, 0.0, 0.0)):
+    """States built only from the atom-centred Gaussian-type functions (no noise), evaluated at r + shift,
+    together with their exact Cartesian gradients.  Returns numpy (psi, [dpsi_x, dpsi_y, dpsi_z]) with the
+    collinear layout [nk][nspin][nbands][npts].  The coefficients depend on the seed only, so shifted
+    copies describe the same states translated by -shift (used to check forces by finite differences)."""
+    g = system.grid
+    rng = np.random.default_rng(seed)
+    alpha = [0.6, 0.9, 0.5, 0.7]
+    xs = [np.arange(g.n[a]) * g.h[a] + g.origin[a] + shift[a] for a in range(3)]
+    Z, Y, X = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
+    X, Y, Z = X.reshape(-1), Y.reshape(-1), Z.reshape(-1)
+    imgs = [(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)] if g.periodic else [(0, 0, 0)]
+    nat = len(system.atoms)
+    out = np.zeros((system.nk, system.nspin, nbands, g.npts), dtype=np.complex128)
+    dout = [np.zeros_like(out) for _ in range(3)]
+    for ik in range(system.nk):
+        G = np.zeros((nat * 4, g.npts), dtype=np.complex128)
+        dG = [np.zeros_like(G) for _ in range(3)]
+        for ia, at in enumerate(system.atoms):
+            a = alpha[at.species]
+            for T in imgs:
+                Tv = [T[i] * g.L[i] for i in range(3)]
+                d = [X - (at.pos[0] + Tv[0]), Y - (at.pos[1] + Tv[1]), Z - (at.pos[2] + Tv[2])]
+                env = np.exp(-a * (d[0] ** 2 + d[1] ** 2 + d[2] ** 2))
+                ph = np.exp(1j * float(np.dot(system.kpts[ik], Tv)))
+                polys = [np.ones_like(d[0]), d[0], d[1], d[0] * d[2]]
+                dpolys = [[0 * d[0], 0 * d[0], 0 * d[0]], [np.ones_like(d[0]), 0 * d[0], 0 * d[0]],
+                          [0 * d[0], np.ones_like(d[0]), 0 * d[0]], [d[2], 0 * d[0], d[0]]]
+                for p in range(4):
+                    G[ia * 4 + p] += ph * polys[p] * env
+                    for c in range(3):
+                        dG[c][ia * 4 + p] += ph * (dpolys[p][c] - 2 * a * d[c] * polys[p]) * env
+        for s in range(system.nspin):
+            C = rng.normal(size=(nat * 4, nbands)) + 1j * rng.normal(size=(nat * 4, nbands))
+            out[ik, s] = C.T @ G
+            for c in range(3):
+                dout[c][ik, s] = C.T @ dG[c]
+    return out, dout

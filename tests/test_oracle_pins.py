@@ -410,3 +410,35 @@ def test_coulomb_integrals_against_slater_integrals(which):
     ref_exch = M * M * sum(float(wigner_3j(l, k, l, 0, 0, 0)) ** 2 * F[k] for k in F)
     assert abs(direct / (M * M * F[0]) - 1) < 1.5e-2
     assert abs(exch / ref_exch - 1) < 1.5e-2
+
+
+def test_hubbard_forces_match_finite_difference_of_energy():
+    """Sec. IV: the force from projections of the state gradients equals minus the derivative of E_U
+    with respect to moving the atom, taken here by translating the (analytic) states the opposite way
+    with the sphere map held fixed; fixed U, complex Bloch states, two spin channels."""
+    s = C.periodic_two_atoms()
+    st = O.setup_atoms(s)
+    nb = 5
+    f = np.linspace(0.3, 1.0, nb)[None, None, :].repeat(s.nk, 0).repeat(2, 1)
+    U = [0.4, 0.3]
+    psi, dpsi = synth.analytic_states(s, nb, seed=3)
+    p = O.project(s, st, psi)
+    occ = O.occupations(s, p, f)
+    V = [np.stack([O.potential(occ[I][0][a], U[I]) for a in range(2)]) for I in range(2)]
+    F = O.hubbard_forces(s, st, psi, dpsi, f, V)
+
+    def energy_atom(I, shift):
+        ps, _ = synth.analytic_states(s, nb, seed=3, shift=shift)
+        oc = O.occupations(s, O.project(s, st, ps), f)
+        return O.hubbard_energy(oc[I][0], U[I], 2)
+
+    eps = 1e-4
+    for I in range(2):
+        for i in range(3):
+            sp = [0.0, 0.0, 0.0]
+            sp[i] = eps
+            sm = [0.0, 0.0, 0.0]
+            sm[i] = -eps
+            dE = (energy_atom(I, sp) - energy_atom(I, sm)) / (2 * eps)   # psi(r + s) = atom moved by +s
+            assert abs(F[I, i] + dE) < 1e-7 * max(1.0, abs(dE)), (I, i, F[I, i], -dE)
+    assert np.max(np.abs(F)) > 1e-4
