@@ -165,6 +165,17 @@ dftu_status dftu_apply(dftu_handle h, void* psi_out, dftu_prec prec, int nbands,
 dftu_status dftu_taylor_step(dftu_handle h, void* psi, void* work, dftu_prec prec, int nbands, int64_t ld_band,
                              const double* f, double dt, int order, dftu_stream stream);
 
+/* Hubbard forces (Sec. IV) on every atom, in the form that differentiates the states: with
+ * g_a = <phi_a|d_i psi> and p_a = <phi_a|psi>,
+ *   F_{I,i} = -sum_{spin blocks} sum_{ab} V_ab sum_{k,n} w_k f [conj(g_a) p_b + conj(p_a) g_b]
+ * where V = U_eff (1/2 - n^T) is the potential of the last dftu_acbn0_uj (U_eff held fixed, as in the
+ * paper).  dpsi: host array of three device pointers to d psi/dx, d psi/dy, d psi/dz in the layout of
+ * psi (the caller computes the gradients, e.g. with its finite-difference stencil).  Requires that the
+ * last dftu_project read psi itself, with the same nbands, and dftu_occupations/dftu_acbn0_uj after it.
+ * F_out: host [natoms][3], Hartree/bohr.  Blocking on stream. */
+dftu_status dftu_forces(dftu_handle h, const void* const* dpsi, dftu_prec prec, int nbands, int64_t ld_band,
+                        const double* f, double* F_out, dftu_stream stream);
+
 /* Projection onto ONE atom's orbitals that allocates nothing, for callers that cannot allocate GPU
  * memory (an application or framework that owns the whole device memory pool, a real-time loop where
  * allocation is not allowed, plug-in code that only receives pointers).  It needs no handle: the caller

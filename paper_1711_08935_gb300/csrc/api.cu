@@ -402,6 +402,8 @@ dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, 
     if (e == cudaSuccess) e = dalloc(c, &v.phi_lo, (size_t)phi_off);
     if (e == cudaSuccess) e = dalloc(c, &v.p, (size_t)rowsP * c->max_bands * MT);
     if (e == cudaSuccess) e = dalloc(c, &v.part, (size_t)rowsP * c->max_bands * TM);
+    if (e == cudaSuccess) e = dalloc(c, &v.pgrad, (size_t)3 * rowsP * c->max_bands * MT);
+    if (e == cudaSuccess) e = dalloc(c, &c->d_forces, (size_t)3 * natoms);
     if (e == cudaSuccess) e = dalloc(c, &v.nbar, (size_t)rowsN * c->max_bands * nspecies);
     if (e == cudaSuccess) e = dalloc(c, &v.rho, (size_t)mat);
     if (e == cudaSuccess) e = dalloc(c, &v.pbar, (size_t)mat);
@@ -630,6 +632,33 @@ dftu_status dftu_taylor_step(dftu_handle h, void* psi, void* work, dftu_prec pre
     c->last_stream = st;
     c->proj_ready = c->occ_ready = c->pot_ready = true;
     c->proj_nbands = nbands;
+    return DFTU_OK;
+}
+
+dftu_status dftu_forces(dftu_handle h, const void* const* dpsi, dftu_prec prec, int nbands, int64_t ld_band, const double* f,
+                        double* F_out, dftu_stream stream) {
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c) return DFTU_ERR_INVALID_ARG;
+    if (!c->pot_ready || !c->proj_ready) return fail(c, DFTU_ERR_NOT_READY, "forces: call dftu_project, dftu_occupations and dftu_acbn0_uj first");
+    if (!dpsi || !dpsi[0] || !dpsi[1] || !dpsi[2] || !f || !F_out || (prec != DFTU_C128 && prec != DFTU_C64) ||
+        !valid_stride_args(c, nbands, ld_band) || nbands != c->proj_nbands)
+        return fail(c, DFTU_ERR_INVALID_ARG, "forces: null pointers, bad precision, ld_band < npts or nbands differs from the projected states");
+    Guard g(c->device);
+    int64_t sk, ss, sn;
+    strides(c, nbands, ld_band, sk, ss, sn);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t gstride = (int64_t)c->nk * c->ns * c->max_bands * c->MT;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+        View vg = c->v;
+        vg.p = c->v.pgrad + i * gstride;   // the gradient projections land in their own buffer
+        e = launch_project(vg, dpsi[i], prec, c->f64_mode, nbands, sk, ss, sn, c->variant[prec == DFTU_C64 ? 1 : 0], st);
+    }
+    if (e == cudaSuccess) e = launch_forces(c->v, f, nbands, c->d_forces, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(F_out, c->d_forces, 3 * c->atoms.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "forces");
+    c->last_stream = st;
     return DFTU_OK;
 }
 

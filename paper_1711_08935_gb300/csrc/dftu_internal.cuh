@@ -72,6 +72,7 @@ struct View {
     double2* seg_phase;    // [nseg][nk] exp(+i k.T)
 
     double2* p;            // [nk*ns][max_bands][MT]
+    double2* pgrad;        // [3][nk*ns][max_bands][MT] projections of the state gradients (forces)
     double2* part;         // [nk*ns][max_bands][TM]
     double* nbar;          // collinear [nk*ns][max_bands][nspecies]; non-collinear [nk][max_bands][nspecies]
     double2* rho;          // per atom: collinear [ns][M][M]; non-collinear [2M][2M]   (rho = n^T)
@@ -119,6 +120,7 @@ struct Ctx {
     int* d_color_order = nullptr;
     double* d_coef_one = nullptr;
     double* d_taylor = nullptr;      // [MAX_TAYLOR] complex Taylor coefficients -i dt / j
+    double* d_forces = nullptr;      // [natoms][3]
     std::vector<int> h_coul_set;     // host copies, so hot-path calls never read the device
     std::vector<double> h_fixU;
 };
@@ -167,6 +169,7 @@ cudaError_t launch_apply(const View& v, void* psi, dftu_prec prec, dftu_f64_mode
                          int64_t sk, int64_t ss, int64_t sn, const double* coef, const int* color_order,
                          const std::vector<int>& color_beg, int variant, int accumulate, cudaStream_t st);
 cudaError_t launch_taylor_coefs(double dt, int order, double* coefs, cudaStream_t st);
+cudaError_t launch_forces(const View& v, const double* f, int nbands, double* F, cudaStream_t st);
 cudaError_t launch_project_batch(const BatchLaunch& b, dftu_prec prec, dftu_f64_mode mode, int variant, cudaStream_t st);
 cudaError_t launch_occupations_batch(const BatchLaunch& b, cudaStream_t st);
 cudaError_t launch_acbn0_batch(const BatchLaunch& b, cudaStream_t st);

@@ -237,6 +237,71 @@ __global__ void __launch_bounds__(1024) k_acbn0(View v) { acbn0_block(v); }
 
 __global__ void __launch_bounds__(256) k_acbn0_batch(const View* __restrict__ views) { acbn0_block(views[blockIdx.x]); }
 
+// Hubbard forces (Sec. IV, state-gradient form, U_eff fixed): one CTA per (atom, direction),
+// F = -sum_{blocks} sum_{ab} V_ab sum_{k,n} w f [conj(g_a) p_b + conj(p_a) g_b], g = <phi|d_i psi>.
+__global__ void __launch_bounds__(CTA) k_forces(View v, const double* __restrict__ f, int nbands, double* __restrict__ F) {
+    const int a = blockIdx.x, dir = blockIdx.y;
+    const int M = v.atom_M[a], mo = v.atom_moff[a];
+    const int64_t vo = v.atom_mat_off[a];
+    const int64_t gstride = (int64_t)v.nk * v.ns * v.max_bands * v.MT;
+    const double2* g = v.pgrad + dir * gstride;
+    double acc = 0.0;
+    if (!v.noncollinear) {
+        const int total = v.nk * v.ns * nbands;
+        for (int e = threadIdx.x; e < total; e += blockDim.x) {
+            const int ks = e / nbands, band = e % nbands, k = ks / v.ns, s = ks % v.ns;
+            const double w = v.wk[k] * f[(int64_t)ks * nbands + band];
+            const double2* pr = v.p + ((int64_t)ks * v.max_bands + band) * v.MT + mo;
+            const double2* gr = g + ((int64_t)ks * v.max_bands + band) * v.MT + mo;
+            const double2* Vm = v.V + vo + (int64_t)s * M * M;
+            double part = 0.0;
+            for (int x = 0; x < M; ++x)
+                for (int y = 0; y < M; ++y) {
+                    double2 px = pr[x], py = pr[y], gx = gr[x], gy = gr[y], V = Vm[x * M + y];
+                    // conj(g_x) p_y + conj(p_x) g_y
+                    double re = gx.x * py.x + gx.y * py.y + px.x * gy.x + px.y * gy.y;
+                    double im = gx.x * py.y - gx.y * py.x + px.x * gy.y - px.y * gy.x;
+                    part += V.x * re - V.y * im;
+                }
+            acc += w * part;
+        }
+    } else {
+        const int D = 2 * M;
+        const int total = v.nk * nbands;
+        for (int e = threadIdx.x; e < total; e += blockDim.x) {
+            const int k = e / nbands, band = e % nbands;
+            const double w = v.wk[k] * f[(int64_t)k * nbands + band];
+            double part = 0.0;
+            for (int x = 0; x < D; ++x)
+                for (int y = 0; y < D; ++y) {
+                    const int cx = x / M, mx = x % M, cy = y / M, my = y % M;
+                    double2 px = v.p[((int64_t)(k * 2 + cx) * v.max_bands + band) * v.MT + mo + mx];
+                    double2 py = v.p[((int64_t)(k * 2 + cy) * v.max_bands + band) * v.MT + mo + my];
+                    double2 gx = g[((int64_t)(k * 2 + cx) * v.max_bands + band) * v.MT + mo + mx];
+                    double2 gy = g[((int64_t)(k * 2 + cy) * v.max_bands + band) * v.MT + mo + my];
+                    double2 V = v.V[vo + x * D + y];
+                    double re = gx.x * py.x + gx.y * py.y + px.x * gy.x + px.y * gy.y;
+                    double im = gx.x * py.y - gx.y * py.x + px.x * gy.y - px.y * gy.x;
+                    part += V.x * re - V.y * im;
+                }
+            acc += w * part;
+        }
+    }
+    __shared__ double red[CTA];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) F[a * 3 + dir] = -((!v.noncollinear && v.ns == 1) ? 2.0 : 1.0) * red[0];
+}
+
+cudaError_t launch_forces(const View& v, const double* f, int nbands, double* F, cudaStream_t st) {
+    k_forces<<<dim3(v.natoms, 3), CTA, 0, st>>>(v, f, nbands, F);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_nbar(const View& v, int nbands, cudaStream_t st) {
     int rows = v.noncollinear ? v.nk : v.nk * v.ns;
     int64_t n = (int64_t)rows * nbands;

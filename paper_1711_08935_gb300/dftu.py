@@ -33,7 +33,7 @@ EXPORTED = ["dftu_create", "dftu_setup_atoms", "dftu_get_sphere", "dftu_coulomb_
             "dftu_set_kernel_variant", "dftu_kernel_variants", "dftu_project_sphere_noalloc",
             "dftu_taylor_step", "dftu_batch_create", "dftu_batch_bind", "dftu_batch_project",
             "dftu_batch_occupations", "dftu_batch_acbn0_uj", "dftu_batch_apply", "dftu_batch_last_error",
-            "dftu_batch_destroy"]
+            "dftu_batch_destroy", "dftu_forces"]
 
 
 class DftuGrid(C.Structure):
@@ -87,6 +87,7 @@ def load() -> C.CDLL:
         "dftu_batch_apply": [vp, vp, i32, vp],
         "dftu_batch_last_error": [vp],
         "dftu_batch_destroy": [vp],
+        "dftu_forces": [vp, C.POINTER(vp), i32, i32, i64, vp, dp, vp],
         "dftu_get_results": [vp, dp, dp, dp, dp, dp, vp],
         "dftu_get_renormalized": [vp, dp, dp, vp],
         "dftu_get_projections": [vp, dp, vp],
@@ -255,6 +256,18 @@ class Handle:
             cp = C.c_void_p(coef.data_ptr())
         self._check(self.lib.dftu_apply(self.h, C.c_void_p(psi.data_ptr()), prec, nb, ld, cp, 1 if accumulate else 0,
                                         _stream_ptr(stream, self.device)))
+
+    def forces(self, dpsi: Sequence[torch.Tensor], f: torch.Tensor, stream=None) -> np.ndarray:
+        """Hubbard forces [natoms][3] (Hartree/bohr) from the gradients of the last projected states."""
+        prec, nb, ld = self._psi_args(dpsi[0])
+        for d in dpsi:
+            if d.shape != dpsi[0].shape or d.dtype != dpsi[0].dtype or not d.is_contiguous():
+                raise ValueError("the three gradients must share shape, dtype and layout")
+        arr = (C.c_void_p * 3)(*[d.data_ptr() for d in dpsi])
+        F = np.zeros((self.natoms, 3))
+        self._check(self.lib.dftu_forces(self.h, arr, prec, nb, ld, C.c_void_p(f.data_ptr()), _dp(F),
+                                         _stream_ptr(stream, self.device)))
+        return F
 
     def taylor_step(self, psi: torch.Tensor, work: torch.Tensor, f: torch.Tensor, dt: float, order: int = 4, stream=None):
         prec, nb, ld = self._psi_args(psi)

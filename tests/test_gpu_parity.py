@@ -268,3 +268,27 @@ def test_every_kernel_variant_matches_oracle(dtype):
         got = t.to(torch.complex128).cpu().numpy()
         assert rel(got, ref["psi_out"]) < (1e-12 if fp64 else 1e-6), var
         h.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+def test_hubbard_forces_match_oracle(dtype):
+    """Sec. IV forces from the projections of the state gradients (fixed U), against the oracle."""
+    s = C.periodic_two_atoms()
+    st = O.setup_atoms(s)
+    nb = 6
+    psi, dpsi = synth.analytic_states(s, nb, seed=5)
+    f = np.linspace(0.2, 1.0, nb)[None, None, :].repeat(s.nk, 0).repeat(2, 1)
+    U = [(0.4, 0.05), (0.3, 0.02)]
+    occ = O.occupations(s, O.project(s, st, psi), f)
+    V = [np.stack([O.potential(occ[I][0][a], U[I][0] - U[I][1]) for a in range(2)]) for I in range(2)]
+    Fref = O.hubbard_forces(s, st, psi, dpsi, f, V)
+    h = dftu.handle_for_system(s, nb)
+    for I, (u, j) in enumerate(U):
+        h.set_u(I, u, j)
+    t = torch.from_numpy(psi).cuda().to(dtype)
+    g = [torch.from_numpy(d).cuda().to(dtype) for d in dpsi]
+    fd = torch.from_numpy(f).cuda()
+    h.project(t); h.occupations(fd); h.acbn0_uj()
+    F = h.forces(g, fd)
+    assert np.max(np.abs(F - Fref)) < (1e-12 if dtype == torch.complex128 else 2e-6) * np.max(np.abs(Fref))
+    assert np.max(np.abs(Fref)) > 1e-5
