@@ -95,6 +95,15 @@ dftu_status dftu_create(dftu_handle* out, const dftu_grid* grid, int nk, const d
 dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, int nspecies,
                              const dftu_radial* radials, int* npts_out);
 
+/* Sphere radii by the second and third methods of Sec. II (the first, the pseudopotential's non-local
+ * cut-off, needs a pseudopotential the library does not read).  Host functions; no device work.
+ *   dftu_radius_cell:      the smallest edge n_a h_a of the cell.
+ *   dftu_radius_threshold: the radius beyond which the tabulated radial function stays below the
+ *                          threshold in magnitude: (i + 1) dr for the last node i with |R_i| >= threshold
+ *                          (0 when no node reaches it; -1 for an invalid table). */
+double dftu_radius_cell(const dftu_grid* grid);
+double dftu_radius_threshold(const dftu_radial* radial, double threshold);
+
 /* Copy atom `atom`'s sphere map to host arrays in canonical order (z outer, y, x inner, ascending
  * unfolded coordinates): idx_out [npts] wrapped linear index, image_out [npts][3] lattice image in
  * cells, phi_out [npts][M] orthonormal orbitals (any of the three may be NULL).  Blocking. */

@@ -138,6 +138,18 @@ def real_ylm(l: int, d: np.ndarray, r: np.ndarray) -> np.ndarray:
     return Y
 
 
+def radius_from_threshold(dr: float, table: np.ndarray, threshold: float) -> float:
+    """Third radius method of Sec. II: the sphere ends where the radial function drops below the
+    threshold for good, i.e. at (i + 1) dr for the last node i with |R_i| >= threshold."""
+    above = np.nonzero(np.abs(np.asarray(table)) >= threshold)[0]
+    return 0.0 if len(above) == 0 else float((above[-1] + 1) * dr)
+
+
+def radius_from_cell(grid) -> float:
+    """Second radius method of Sec. II: the smallest dimension of the cell."""
+    return float(min(grid.n[a] * grid.h[a] for a in range(3)))
+
+
 def raw_orbitals(atom, radial, smap) -> np.ndarray:
     """phi_m(j) = R(|d_j|) Y_lm(d_j) on the sphere points, [S, 2l+1] (pseudo-atomic orbital of Sec. II)."""
     Rv = radial_value(radial.dr, radial.R, smap["r"])

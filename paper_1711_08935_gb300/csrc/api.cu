@@ -427,6 +427,20 @@ dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, 
     return DFTU_OK;
 }
 
+double dftu_radius_cell(const dftu_grid* grid) {
+    if (!grid) return -1.0;
+    double r = grid->n[0] * grid->h[0];
+    for (int d = 1; d < 3; ++d) r = std::min(r, grid->n[d] * grid->h[d]);
+    return r;
+}
+
+double dftu_radius_threshold(const dftu_radial* radial, double threshold) {
+    if (!radial || !radial->R || radial->nr < 1 || !(radial->dr > 0.0) || !(threshold > 0.0)) return -1.0;
+    for (int i = radial->nr - 1; i >= 0; --i)
+        if (std::fabs(radial->R[i]) >= threshold) return (i + 1) * radial->dr;
+    return 0.0;
+}
+
 dftu_status dftu_get_sphere(dftu_handle h, int atom, int32_t* idx_out, int32_t* image_out, double* phi_out) {
     Ctx* c = reinterpret_cast<Ctx*>(h);
     if (!c) return DFTU_ERR_INVALID_ARG;

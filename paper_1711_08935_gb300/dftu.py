@@ -33,7 +33,7 @@ EXPORTED = ["dftu_create", "dftu_setup_atoms", "dftu_get_sphere", "dftu_coulomb_
             "dftu_set_kernel_variant", "dftu_kernel_variants", "dftu_project_sphere_noalloc",
             "dftu_taylor_step", "dftu_batch_create", "dftu_batch_bind", "dftu_batch_project",
             "dftu_batch_occupations", "dftu_batch_acbn0_uj", "dftu_batch_apply", "dftu_batch_last_error",
-            "dftu_batch_destroy", "dftu_forces"]
+            "dftu_batch_destroy", "dftu_forces", "dftu_radius_cell", "dftu_radius_threshold"]
 
 
 class DftuGrid(C.Structure):
@@ -88,6 +88,8 @@ def load() -> C.CDLL:
         "dftu_batch_last_error": [vp],
         "dftu_batch_destroy": [vp],
         "dftu_forces": [vp, C.POINTER(vp), i32, i32, i64, vp, dp, vp],
+        "dftu_radius_cell": [C.POINTER(DftuGrid)],
+        "dftu_radius_threshold": [C.POINTER(DftuRadial), d],
         "dftu_get_results": [vp, dp, dp, dp, dp, dp, vp],
         "dftu_get_renormalized": [vp, dp, dp, vp],
         "dftu_get_projections": [vp, dp, vp],
@@ -107,6 +109,8 @@ def load() -> C.CDLL:
     L.dftu_last_error.restype = C.c_char_p
     L.dftu_destroy.restype = None
     L.dftu_batch_last_error.restype = C.c_char_p
+    L.dftu_radius_cell.restype = C.c_double
+    L.dftu_radius_threshold.restype = C.c_double
     L.dftu_batch_destroy.restype = None
     _lib = L
     return L
@@ -385,6 +389,19 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def radius_cell(grid) -> float:
+    """Second method of Sec. II: the smallest cell edge."""
+    g = DftuGrid((C.c_int * 3)(*grid.n), (C.c_double * 3)(*grid.h), (C.c_double * 3)(*grid.origin), 1 if grid.periodic else 0)
+    return load().dftu_radius_cell(C.byref(g))
+
+
+def radius_threshold(radial, threshold: float) -> float:
+    """Third method of Sec. II: where the radial function falls below `threshold` for good."""
+    R = np.ascontiguousarray(radial.R, dtype=np.float64)
+    r = DftuRadial(len(R), radial.dr, _dp(R))
+    return load().dftu_radius_threshold(C.byref(r), float(threshold))
 
 
 def handle_for_system(system, max_bands: int, device: int = 0) -> Handle:

@@ -20,7 +20,7 @@ def lib():
 def test_header_declarations_are_exported(lib):
     from paper_1711_08935_gb300 import dftu
     hdr = open(os.path.join(ROOT, "include", "dftu.h")).read()
-    declared = set(re.findall(r"^\s*(?:dftu_status|int|void|const char\*)\s+(dftu_\w+)\s*\(", hdr, re.M))
+    declared = set(re.findall(r"^\s*(?:dftu_status|int|void|double|const char\*)\s+(dftu_\w+)\s*\(", hdr, re.M))
     assert declared == set(dftu.EXPORTED)
     out = subprocess.run(["nm", "-D", "--defined-only", dftu.LIB_PATH], capture_output=True, text=True).stdout
     exported = {l.split()[-1] for l in out.splitlines() if l.split() and l.split()[-1].startswith("dftu_")}
@@ -52,3 +52,27 @@ def test_create_without_gpu_fails_cleanly(lib):
     w = (C.c_double * 1)(1.0)
     st = lib.dftu_create(C.byref(h), C.byref(g), 1, k, w, 0, 4, 0)
     assert st == dftu.DFTU_ERR_INVALID_ARG and not h.value
+
+
+def test_radius_methods_match_oracle(lib):
+    """Sec. II radius methods 2 and 3 (host functions of the library) against the oracle's statement,
+    and the threshold radius against the analytic tail of a hydrogen-like 3d radial."""
+    import math
+    import numpy as np
+    from oracle import dftu_oracle as O
+    from paper_1711_08935_gb300 import dftu, synth
+    g = synth.Grid((40, 48, 36), (0.3, 0.25, 0.35), periodic=True)
+    assert dftu.radius_cell(g) == O.radius_from_cell(g) == min(12.0, 12.0, 12.6)
+    rad = synth.hydrogenic_radial(3, 2, 4.0)
+    for thr in (1e-2, 1e-3, 1e-5):
+        r_lib = dftu.radius_threshold(rad, thr)
+        assert r_lib == O.radius_from_threshold(rad.dr, rad.R, thr)
+        # R_32 ~ c (8r/3)^2 exp(-4r/3) is monotone beyond its maximum at r = 1.5: the crossing is the root
+        c = (8.0 / 3.0) ** 1.5 * math.sqrt(1 / (6 * 120))
+        f = lambda r: c * (8 * r / 3) ** 2 * math.exp(-4 * r / 3) - thr
+        lo, hi = 1.5, 12.0
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            lo, hi = (mid, hi) if f(mid) > 0 else (lo, mid)
+        assert abs(r_lib - lo) <= 2 * rad.dr
+    assert dftu.radius_threshold(rad, 1e9) == 0.0
