@@ -491,6 +491,69 @@ def taylor_step(system, atoms_setup, psi, f, dt, coulomb=None, fixed_u=None, ord
 
 
 # ------------------------------------------------------------------------------------------------
+# Gauge-invariant Hubbard operator V_U^A = exp(-i A.r) V_U exp(i A.r) (Sec. V, Eq. 16) and its current
+# ------------------------------------------------------------------------------------------------
+# Reading: on atom I's sphere r = R_I + d_j; the factor exp(+-i A.R_I) cancels between the gather and
+# the scatter of the same projector and in the occupations, so the operator is the plain one with the
+# orbitals phi_m(d) exp(-i A.d): the gather multiplies by exp(+i A.d_j), the scatter by exp(-i A.d_j).
+
+def gauge_phases(smap, A) -> np.ndarray:
+    """exp(+i A.d_j) for every sphere point (d_j = unfolded position minus the atom centre)."""
+    return np.exp(1j * (smap["d"] @ np.asarray(A, dtype=np.float64)))
+
+
+def project_gauge(system, atoms_setup, psi, A) -> List[np.ndarray]:
+    """p^A = <phi_m exp(-i A.d)|psi> = dV sum_j phi_m(j) exp(+i A.d_j) exp(+i k.T_j) psi(idx_j)."""
+    dV = system.grid.dV
+    out = []
+    for sm in atoms_setup:
+        nk, ns, nb = psi.shape[:3]
+        g = gauge_phases(sm, A)
+        p = np.zeros((nk, ns, nb, sm["phi"].shape[1]), dtype=np.complex128)
+        for ik in range(nk):
+            ph = phases(system, sm, system.kpts[ik]) * g
+            for s in range(ns):
+                p[ik, s] = dV * ((psi[ik, s][:, sm["idx"]] * ph[None, :]) @ sm["phi"])
+        out.append(p)
+    return out
+
+
+def apply_gauge(system, atoms_setup, psi, p_atoms, V_atoms, A, coef=1.0) -> np.ndarray:
+    """Eq. (16): psi(idx_j) += coef exp(-i k.T_j) exp(-i A.d_j) sum_m phi_m(j) (V p)_m."""
+    out = psi.copy()
+    for I, sm in enumerate(atoms_setup):
+        g = np.conj(gauge_phases(sm, A))
+        for ik in range(psi.shape[0]):
+            ph = np.conj(phases(system, sm, system.kpts[ik])) * g
+            for s in range(psi.shape[1]):
+                Vp = p_atoms[I][ik, s] @ V_atoms[I][s].T
+                upd = coef * (Vp @ sm["phi"].T) * ph[None, :]
+                np.add.at(out[ik, s], (slice(None), sm["idx"]), upd)
+    return out
+
+
+def hubbard_current(system, atoms_setup, psi, f, V_atoms, A) -> np.ndarray:
+    """Hubbard term of the current (Sec. V, Eq. 17), read as J = sum w f <psi| -i [r, V_U^A] |psi>: the
+    printed <psi|[r, V]|psi> + c.c. vanishes for a Hermitian V, so the factor i of the velocity operator
+    is restored.  With q^{(a)}_m = <phi_m exp(-i A.d)| d_a psi> this is
+    J_a = -i sum w f sum_{mm'} V_{mm'} [conj(q_m) p_m' - conj(p_m) q_m'] (real), and equals dE_U/dA at
+    fixed states.  Collinear/unpolarised; returns [3]."""
+    p = project_gauge(system, atoms_setup, psi, A)
+    wf = np.asarray(system.wk)[:, None, None] * f
+    mult = 2.0 if system.nspin == 1 else 1.0
+    J = np.zeros(3)
+    for a in range(3):
+        for I, sm in enumerate(atoms_setup):
+            sm_d = dict(sm)
+            sm_d["phi"] = sm["phi"] * sm["d"][:, a:a + 1]
+            q = project_gauge(system, [sm_d], psi, A)[0]
+            X = (np.einsum("ksn,ksnm,ksnq,smq->", wf, np.conj(q), p[I], V_atoms[I])
+                 - np.einsum("ksn,ksnm,ksnq,smq->", wf, np.conj(p[I]), q, V_atoms[I]))
+            J[a] += mult * float(np.real(-1j * X))
+    return J
+
+
+# ------------------------------------------------------------------------------------------------
 # Hubbard forces (Sec. IV): F = -dE_U/dR with dn/dR from projections of the state gradients
 # ------------------------------------------------------------------------------------------------
 

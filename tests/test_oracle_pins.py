@@ -442,3 +442,53 @@ def test_hubbard_forces_match_finite_difference_of_energy():
             dE = (energy_atom(I, sp) - energy_atom(I, sm)) / (2 * eps)   # psi(r + s) = atom moved by +s
             assert abs(F[I, i] + dE) < 1e-7 * max(1.0, abs(dE)), (I, i, F[I, i], -dE)
     assert np.max(np.abs(F)) > 1e-4
+
+
+def test_gauge_operator_equals_literal_definition_on_isolated_box():
+    """Eq. (16) read literally on an isolated box, exp(-i A.r) V_U exp(+i A.r) with r the grid position,
+    equals the atom-relative form the oracle uses (the exp(+-i A.R_I) factors cancel)."""
+    g = synth.Grid((18, 16, 17), (0.4, 0.4, 0.4), (0.2, -0.1, 0.3), periodic=False)
+    s = synth.System(g, [synth.Atom((3.1, 2.9, 3.4), 0, 2, 2.6), synth.Atom((4.3, 3.5, 3.0), 1, 1, 2.4)],
+                     [synth.hydrogenic_radial(3, 2, 3.0), synth.hydrogenic_radial(2, 1, 3.5)],
+                     np.zeros((1, 3)), np.ones(1), nspin=2)
+    st = O.setup_atoms(s)
+    psi = C.states_np(s, 4, seed=2)
+    f = np.full((1, 2, 4), 0.7)
+    A = np.array([0.31, -0.17, 0.22])
+    occ = O.occupations(s, O.project_gauge(s, st, psi, A), f)
+    V = [np.stack([O.potential(occ[I][0][a], 0.3) for a in range(2)]) for I in range(2)]
+    out = O.apply_gauge(s, st, psi, O.project_gauge(s, st, psi, A), V, A)
+    xs = [np.arange(g.n[a]) * g.h[a] + g.origin[a] for a in range(3)]
+    Z, Y, X = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
+    r = np.stack([X.reshape(-1), Y.reshape(-1), Z.reshape(-1)], 1)
+    U = np.exp(1j * (r @ A))
+    lit = psi * 0
+    pu = O.project(s, st, psi * U)
+    lit = O.apply(s, st, np.zeros_like(psi), pu, V) * np.conj(U)
+    assert np.max(np.abs((out - psi) - lit)) < 1e-13 * np.max(np.abs(lit))
+
+
+def test_hubbard_current_is_energy_derivative_in_A():
+    """The Hubbard current (Sec. V, Eq. 17, with the velocity operator's factor i) equals dE_U/dA at
+    fixed states, by central differences; periodic complex Bloch states."""
+    s = C.periodic_two_atoms()
+    st = O.setup_atoms(s)
+    psi = C.states_np(s, 5, seed=8)
+    f = np.linspace(0.3, 1.0, 5)[None, None, :].repeat(s.nk, 0).repeat(2, 1)
+    U = [0.5, 0.35]
+    A0 = np.array([0.05, -0.02, 0.03])
+
+    def E(A):
+        oc = O.occupations(s, O.project_gauge(s, st, psi, A), f)
+        return sum(O.hubbard_energy(oc[I][0], U[I], 2) for I in range(2))
+
+    oc = O.occupations(s, O.project_gauge(s, st, psi, A0), f)
+    V = [np.stack([O.potential(oc[I][0][a], U[I]) for a in range(2)]) for I in range(2)]
+    J = O.hubbard_current(s, st, psi, f, V, A0)
+    eps = 1e-5
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = eps
+        dE = (E(A0 + e) - E(A0 - e)) / (2 * eps)
+        assert abs(J[a] - dE) < 1e-8 * max(1.0, abs(dE)), (a, J[a], dE)
+    assert np.max(np.abs(J)) > 1e-6
