@@ -2,9 +2,10 @@
 
 One step = one pass of the whole hot path over the oxide supercell (periodic 96^3 grid at 0.25 bohr,
 8 transition-metal d shells + 8 oxygen p shells, 256 bands, 8 k-points, collinear spin):
-    project -> occupations (n, Nbar, Pbar) -> ACBN0 U, J, E_U, V -> apply (psi += V_U psi, in place)
-through the C ABI.  The metric is algorithmic GB/s of that pass: every sphere point of every state is
-read by the projection and read + written by the apply (complex128: 16 B per point).
+    project -> occupations (n, Nbar, Pbar) -> ACBN0 U, J, E_U, V -> apply (H psi += V_U psi)
+through the C ABI, the apply accumulating into a separate H psi buffer so that every step sees the
+same states.  The metric is algorithmic GB/s of that pass: every sphere point of every state is read
+by the projection and read + written by the apply (complex128: 16 B per point).
 
 Prints ONE JSON line (rank 0).  --impl reference times the CPU FP64 oracle on a bounded sample of the
 same workload instead.  Under torchrun every rank runs an independent replica (the pass has no
@@ -159,15 +160,17 @@ def run_ours(args):
     dJ = float(np.max(np.abs(r64["J"] - r32["J"]))) * dftu.HARTREE_EV
     dE = abs(r64["EU"] - r32["EU"]) * dftu.HARTREE_EV
 
-    def step(x):
+    # H psi accumulates V_U psi (Eq. 6) in its own buffer, as in a Hamiltonian application: every step
+    # then works on the same states, and the apply reads and writes as many bytes as an in-place one.
+    def step(x, out):
         h.project(x)
         h.occupations(f)
         h.acbn0_uj()
-        h.apply(x)
+        h.apply(out)
 
-    def timed(x, steps, warmup):
+    def timed(x, out, steps, warmup):
         for _ in range(warmup):
-            step(x)
+            step(x, out)
         torch.cuda.synchronize()
         if ws > 1:
             torch.distributed.barrier()
@@ -186,7 +189,7 @@ def run_ours(args):
             h.acbn0_uj()
             e2.record(stream)
             e3.record(stream)
-            h.apply(x)
+            h.apply(out)
             e4.record(stream)
         end.record(stream)
         torch.cuda.synchronize()
@@ -201,18 +204,23 @@ def run_ours(args):
         for which, var in enumerate(int(x) for x in args.variants.split(",")):
             h.set_kernel_variant(which, var)
         tuned["fixed"] = args.variants
-    elif not args.no_tune:
+    hpsi = torch.zeros_like(psi)
+    if not args.variants and not args.no_tune:
         from paper_1711_08935_gb300.autotune import autotune
-        tuned["c128"] = autotune(h, psi)
-        tuned["c64"] = autotune(h, psi32)
+        tuned["c128"] = autotune(h, psi, out=hpsi)
+        hpsi32 = torch.zeros_like(psi32)
+        tuned["c64"] = autotune(h, psi32, out=hpsi32)
+        del hpsi32
         h.project(psi); h.occupations(f); h.acbn0_uj()
     clocks = ClockSampler(local)
     clocks.start()
-    ms64, proj64, small64, app64 = timed(psi, args.steps, args.warmup)
+    ms64, proj64, small64, app64 = timed(psi, hpsi, args.steps, args.warmup)
     clk = clocks.stop()
-    del psi
+    del psi, hpsi
     torch.cuda.empty_cache()
-    ms32, proj32, small32, app32 = timed(psi32, args.steps, args.warmup)
+    hpsi32 = torch.zeros_like(psi32)
+    ms32, proj32, small32, app32 = timed(psi32, hpsi32, args.steps, args.warmup)
+    del hpsi32
     status = h.sync_status()
 
     pb64, ab64 = algorithmic_bytes(npts, nb, s.nk, 2, 16, orb_bytes)
@@ -455,13 +463,16 @@ def run_molecules(args):
 
     batch = dftu.Batch(hs)
     batch.bind(psis, fs)
+    # the batch applies in place onto the bound states, so each step is a first-order real-time update
+    # psi += -i dt V_U psi (dt = 0.01 a.u.), which keeps the states bounded over the repeated steps
+    cdt = torch.tensor([-0.01j], dtype=torch.complex128, device=dev)
 
     def batched():
-        batch.project(); batch.occupations(); batch.acbn0_uj(); batch.apply()
+        batch.project(); batch.occupations(); batch.acbn0_uj(); batch.apply(cdt)
 
     def one_by_one(idx, ps):
         for i in idx:
-            hs[i].project(ps[i]); hs[i].occupations(fs[i]); hs[i].acbn0_uj(); hs[i].apply(ps[i])
+            hs[i].project(ps[i]); hs[i].occupations(fs[i]); hs[i].acbn0_uj(); hs[i].apply(ps[i], cdt)
 
     allidx = list(range(len(systems)))
     clocks = ClockSampler(0)
@@ -477,12 +488,12 @@ def run_molecules(args):
     ms_sub64 = time_it(lambda: one_by_one(sub, ps64), max(1, args.steps // 2), 1)
     bsub = dftu.Batch([hs[i] for i in sub])
     bsub.bind(p64, [fs[i] for i in sub])
-    ms_sub64_b = time_it(lambda: (bsub.project(), bsub.occupations(), bsub.acbn0_uj(), bsub.apply()), args.steps, 1)
+    ms_sub64_b = time_it(lambda: (bsub.project(), bsub.occupations(), bsub.acbn0_uj(), bsub.apply(cdt)), args.steps, 1)
     bsub.close()
     del p64, ps64
     bsub32 = dftu.Batch([hs[i] for i in sub])
     bsub32.bind([psis[i] for i in sub], [fs[i] for i in sub])
-    ms_sub32_b = time_it(lambda: (bsub32.project(), bsub32.occupations(), bsub32.acbn0_uj(), bsub32.apply()), args.steps, 1)
+    ms_sub32_b = time_it(lambda: (bsub32.project(), bsub32.occupations(), bsub32.acbn0_uj(), bsub32.apply(cdt)), args.steps, 1)
     bsub32.close()
     peak, src = measured_peaks()
     val = pass_bytes(allidx, 8) / (ms_b * 1e-3) / 1e9
@@ -521,26 +532,27 @@ def run_nc(args):
     r64 = h.results()
     h.project(psi32); h.occupations(f); h.acbn0_uj()
     r32 = h.results()
-    autotune(h, psi)
-    autotune(h, psi32)
+    hpsi, hpsi32 = torch.zeros_like(psi), torch.zeros_like(psi32)   # H psi buffers: the states stay as generated
+    autotune(h, psi, out=hpsi)
+    autotune(h, psi32, out=hpsi32)
 
-    def t(x):
+    def t(x, out):
         for _ in range(args.warmup):
-            h.project(x); h.occupations(f); h.acbn0_uj(); h.apply(x)
+            h.project(x); h.occupations(f); h.acbn0_uj(); h.apply(out)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(args.steps):
-            h.project(x); h.occupations(f); h.acbn0_uj(); h.apply(x)
+            h.project(x); h.occupations(f); h.acbn0_uj(); h.apply(out)
         e1.record()
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / args.steps
 
     clocks = ClockSampler(0)
     clocks.start()
-    ms64 = t(psi)
+    ms64 = t(psi, hpsi)
     clk = clocks.stop()
-    ms32 = t(psi32)
+    ms32 = t(psi32, hpsi32)
     S = _sphere_bytes(h, len(s.atoms))
     b64 = 3 * S * 16 * nb * s.nk * 2
     peak, src = measured_peaks()
@@ -554,6 +566,99 @@ def run_nc(args):
                        "max_abs_dn": max(float(np.max(np.abs(a - b))) for a, b in zip(r64["n"], r32["n"])),
                        "max_dU_eV": float(np.max(np.abs(r64["U"] - r32["U"]))) * dftu.HARTREE_EV},
         "peak": peak, "peak_source": src, "frac_of_peak": round(b64 / (ms64 * 1e-3) / 1e9 / peak, 4), "clocks": clk}))
+
+
+def run_gauge(args):
+    """The headline oxide pass with the gauge-invariant operator of Sec. V (Eq. 16): every step sets the
+    vector potential (phase table kernel), projects with the phases, builds occupations and U/J, and
+    applies with the conjugate phases; the Hubbard current of Eq. (17) is timed separately.  The plain
+    pass (tuned shapes) runs on the same states for comparison."""
+    import torch
+    from paper_1711_08935_gb300 import dftu, synth
+    dev = torch.device("cuda", 0)
+    s = synth.oxide_system(n=args.grid, nk=args.nkgrid)
+    nb = args.nbands
+    psi = synth.make_states(s, nb, seed=2, device=dev, spin_bias=synth.afm_spin_bias(s))
+    f = torch.from_numpy(synth.step_occupations(s.nk, 2, nb, nb // 2)).to(dev)
+    h = dftu.handle_for_system(s, nb)
+    _coulomb_all(h, s)
+    npts = [h.lib.dftu_atom_points(h.h, i) for i in range(len(s.atoms))]
+    orb_bytes = sum(n * (2 * a.l + 1) * 8 for n, a in zip(npts, s.atoms))
+    pb, ab = algorithmic_bytes(npts, nb, s.nk, 2, 16, orb_bytes)
+    gauge_bytes = int(sum(npts)) * 16                 # the phase table, read once per projection and apply
+    A = torch.tensor([0.3, -0.2, 0.25], dtype=torch.float64, device=dev)
+    psi32 = psi.to(torch.complex64)
+    hpsi = torch.zeros_like(psi)                     # H psi accumulates V_U psi; the states stay as generated
+    from paper_1711_08935_gb300.autotune import autotune
+    h.project(psi); h.occupations(f); h.acbn0_uj()     # the tuner's apply needs a potential
+    tuned = {"c128": autotune(h, psi, out=hpsi)}
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(x, out, gauge, steps, warmup):
+        def one(evs=None):
+            if gauge:
+                h.set_vector_potential(A)
+            if evs: evs[0].record(stream)
+            h.project(x)
+            if evs: evs[1].record(stream)
+            h.occupations(f); h.acbn0_uj()
+            if evs: evs[2].record(stream)
+            h.apply(out)
+            if evs: evs[3].record(stream)
+        for _ in range(warmup):
+            one()
+        torch.cuda.synchronize()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps):
+            one(ev[i])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return (e0.elapsed_time(e1) / steps, statistics.mean(e[0].elapsed_time(e[1]) for e in ev),
+                statistics.mean(e[2].elapsed_time(e[3]) for e in ev))
+
+    ms_plain, pr_plain, ap_plain = timed(psi, hpsi, False, args.steps, args.warmup)
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms_g, pr_g, ap_g = timed(psi, hpsi, True, args.steps, args.warmup)
+    clk = clocks.stop()
+    # Hubbard current: three projections onto the displaced orbitals + the contraction, blocking
+    h.set_vector_potential(A); h.project(psi); h.occupations(f); h.acbn0_uj()
+    for _ in range(2):
+        h.hubbard_current(psi, f)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps = max(2, args.steps // 2)
+    for _ in range(reps):
+        J = h.hubbard_current(psi, f)
+    cur_ms = (time.perf_counter() - t0) * 1e3 / reps
+    del hpsi
+    hpsi32 = torch.zeros_like(psi32)
+    ms_g32, pr_g32, ap_g32 = timed(psi32, hpsi32, True, args.steps, args.warmup)
+    status = h.sync_status()
+    peak, src = measured_peaks()
+    step_bytes = pb + ab + 2 * gauge_bytes
+    dom_is_apply = ap_g >= pr_g
+    dom_b = (ab + gauge_bytes) if dom_is_apply else (pb + gauge_bytes)
+    dom_ms = ap_g if dom_is_apply else pr_g
+    achieved = dom_b / (dom_ms * 1e-3) / 1e9
+    print(json.dumps({
+        "metric": METRIC, "value": round(step_bytes / (ms_g * 1e-3) / 1e9, 2), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_g, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c128 states; FP32-pair arithmetic, gauge phases as FP32 pairs", "data": "synthetic",
+        "config": {"workload": "gauge-invariant pass (Sec. V): oxide supercell 96^3 h=0.25, 8 TM(3d,R4.5)+8 O(2p,R3.5), "
+                               "256 bands, 8 k, collinear, A=(0.3,-0.2,0.25) a.u. set every step",
+                   "sphere_points": int(sum(npts)), "l2": "inputs (58 GB of states) far larger than L2; no flush needed"},
+        "roofline": {"bound": "hbm", "kernel": "apply (gauge)" if dom_is_apply else "project (gauge)",
+                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "peak_source": src, "traffic": None, "bytes_per_launch": dom_b},
+        "kernels_ms": {"project_gauge": round(pr_g, 4), "apply_gauge": round(ap_g, 4), "project_plain": round(pr_plain, 4),
+                       "apply_plain": round(ap_plain, 4)},
+        "plain_pass_ms": round(ms_plain, 4), "gauge_overhead": round(ms_g / ms_plain, 3),
+        "current": {"ms": round(cur_ms, 3), "J": [float(x) for x in J], "note": "3 projections + contraction + host copy, blocking"},
+        "fp32_state": {"ms_per_step": round(ms_g32, 4), "project_ms": round(pr_g32, 4), "apply_ms": round(ap_g32, 4)},
+        "tuning": tuned, "gpu_launches": (1 + 2 + 2 + 1 + 1) * args.steps, "device_status": int(status), "clocks": clk}))
 
 
 def run_reference(args):
@@ -606,8 +711,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--variants", default="", help="fixed kernel variants 'p128,p64,a128,a64' instead of tuning")
-    ap.add_argument("--workload", default="oxide", choices=["oxide", "rt", "molecules", "nc"],
-                    help="oxide: the headline pass; rt / molecules / nc: the other workloads, one JSON line each")
+    ap.add_argument("--workload", default="oxide", choices=["oxide", "rt", "molecules", "nc", "gauge"],
+                    help="oxide: the headline pass; rt / molecules / nc / gauge: the other workloads, one JSON line each")
     ap.add_argument("--rt-steps", type=int, default=200)
     ap.add_argument("--copy-streams", type=int, default=4, help="streams for the end-to-end host-to-device copies")
     ap.add_argument("--nsys", type=int, default=256)
@@ -621,6 +726,8 @@ def main():
         run_molecules(args)
     elif args.workload == "nc":
         run_nc(args)
+    elif args.workload == "gauge":
+        run_gauge(args)
     else:
         run_ours(args)
 

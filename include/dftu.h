@@ -174,6 +174,31 @@ dftu_status dftu_apply(dftu_handle h, void* psi_out, dftu_prec prec, int nbands,
 dftu_status dftu_taylor_step(dftu_handle h, void* psi, void* work, dftu_prec prec, int nbands, int64_t ld_band,
                              const double* f, double dt, int order, dftu_stream stream);
 
+/* Gauge-invariant Hubbard operator under a uniform vector potential A (Sec. V, Eq. 16).  Every
+ * localised orbital carries the phase exp(-i A.d), d = r - R_I measured from its own atom (the
+ * atom-relative reading of Eq. 16), so after this call
+ *   dftu_project gives p^A_m = dV sum_j phi_m(j) exp(+i A.d_j) exp(+i k.T_j) psi(idx_j), and
+ *   dftu_apply / dftu_taylor_step scatter with exp(-i A.d_j) exp(-i k.T_j),
+ * while dftu_occupations and dftu_acbn0_uj are unchanged (they read p^A).  A: device pointer to three
+ * FP64 numbers (atomic units, the phase is A.d with d in bohr), read by a kernel on `stream` when it
+ * runs, so a graph may capture this call and replay it after A changes.  A = NULL switches the phases
+ * off.  Either way the handle's projections, occupations and potential are marked stale.
+ * Collinear and unpolarised states only (INVALID_ARG for a non-collinear handle with A != NULL);
+ * dftu_forces returns INVALID_ARG while A is set.  Launches only, no synchronisation. */
+dftu_status dftu_set_vector_potential(dftu_handle h, const double* A, dftu_stream stream);
+
+/* Hubbard contribution to the current (Sec. V, Eq. 17), read as J = sum_{k,n} w_k f <psi| -i [r, V_U^A] |psi>
+ * (the printed commutator expectation plus its conjugate vanishes for a Hermitian V_U; the velocity
+ * operator's factor i is restored).  With q^(a)_m = <phi_m d_a exp(-i A.d)|psi>,
+ *   J_a = mult Im sum_{k,s,n} w_k f sum_{mm'} V_{mm'} [conj(q_m) p_m' - conj(p_m) q_m'],
+ * mult = 2 for unpolarised states, and J = dE_U/dA at fixed states.  p and V are those of the last
+ * dftu_project (which must have read psi itself, with the same nbands and the current vector potential)
+ * and dftu_acbn0_uj.  f: device occupations as for dftu_occupations.  J_out: host [3] (sum over atoms)
+ * and/or J_atom_out: host [natoms][3]; either may be NULL, not both.  Collinear and unpolarised states
+ * only.  Blocking on stream. */
+dftu_status dftu_hubbard_current(dftu_handle h, const void* psi, dftu_prec prec, int nbands, int64_t ld_band,
+                                 const double* f, double* J_out, double* J_atom_out, dftu_stream stream);
+
 /* Hubbard forces (Sec. IV) on every atom, in the form that differentiates the states: with
  * g_a = <phi_a|d_i psi> and p_a = <phi_a|psi>,
  *   F_{I,i} = -sum_{spin blocks} sum_{ab} V_ab sum_{k,n} w_k f [conj(g_a) p_b + conj(p_a) g_b]

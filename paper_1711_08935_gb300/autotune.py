@@ -1,6 +1,7 @@
 """Autotuner for the streaming kernels: times every shape variant of the projection and apply
 kernels (dftu_set_kernel_variant) on the caller's own states with CUDA events and keeps the fastest.
-The apply variants modify the states in place, as the apply always does."""
+The apply variants accumulate into `out` (the caller's H psi buffer), or into psi itself when no
+buffer is given."""
 from __future__ import annotations
 
 import torch
@@ -23,9 +24,10 @@ def _time(fn, reps, stream):
     return e0.elapsed_time(e1) / reps
 
 
-def autotune(h: dftu.Handle, psi: torch.Tensor, reps: int = 3) -> dict:
+def autotune(h: dftu.Handle, psi: torch.Tensor, reps: int = 3, out: torch.Tensor = None) -> dict:
     """Pick the fastest projection and apply variants for psi's precision; returns the timings (ms).
     The handle must already hold a potential (dftu_acbn0_uj) for the apply to run."""
+    target = psi if out is None else out
     stream = torch.cuda.current_stream(psi.device)
     out = {}
     for kind in ("project", "apply"):
@@ -34,7 +36,7 @@ def autotune(h: dftu.Handle, psi: torch.Tensor, reps: int = 3) -> dict:
         times = []
         for v in range(n):
             h.set_kernel_variant(which, v)
-            fn = (lambda: h.project(psi)) if kind == "project" else (lambda: h.apply(psi))
+            fn = (lambda: h.project(psi)) if kind == "project" else (lambda: h.apply(target))
             times.append(_time(fn, reps, stream))
         best = min(range(n), key=lambda i: times[i])
         h.set_kernel_variant(which, best)

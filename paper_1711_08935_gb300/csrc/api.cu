@@ -404,6 +404,12 @@ dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, 
     if (e == cudaSuccess) e = dalloc(c, &v.part, (size_t)rowsP * c->max_bands * TM);
     if (e == cudaSuccess) e = dalloc(c, &v.pgrad, (size_t)3 * rowsP * c->max_bands * MT);
     if (e == cudaSuccess) e = dalloc(c, &c->d_forces, (size_t)3 * natoms);
+    if (e == cudaSuccess) e = dalloc(c, &c->d_current, (size_t)3 * natoms);
+    if (e == cudaSuccess) e = dalloc(c, &v.gauge_d, (size_t)c->S);
+    if (e == cudaSuccess) e = dalloc(c, &v.gauge_f, (size_t)c->S);
+    if (e == cudaSuccess) e = dalloc(c, &v.phid64, (size_t)3 * phi_off);
+    if (e == cudaSuccess) e = dalloc(c, &v.phid_hi, (size_t)3 * phi_off);
+    if (e == cudaSuccess) e = dalloc(c, &v.phid_lo, (size_t)3 * phi_off);
     if (e == cudaSuccess) e = dalloc(c, &v.nbar, (size_t)rowsN * c->max_bands * nspecies);
     if (e == cudaSuccess) e = dalloc(c, &v.rho, (size_t)mat);
     if (e == cudaSuccess) e = dalloc(c, &v.pbar, (size_t)mat);
@@ -419,6 +425,7 @@ dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, 
     e = launch_seg_phases(v, 0);
     if (e == cudaSuccess) e = launch_orbitals(v, d_rtab, d_roff, d_rnr, d_rdr, 0);
     if (e == cudaSuccess) e = launch_lowdin(v, work, 0);
+    if (e == cudaSuccess) e = launch_displaced_orbitals(v, phi_off, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(c, e, "setup_atoms: orbitals");
     if (npts_out)
@@ -554,7 +561,8 @@ dftu_status dftu_project(dftu_handle h, const void* psi, dftu_prec prec, int nba
     int64_t sk, ss, sn;
     strides(c, nbands, ld_band, sk, ss, sn);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    cudaError_t e = launch_project(c->v, psi, prec, c->f64_mode, nbands, sk, ss, sn, c->variant[prec == DFTU_C64 ? 1 : 0], st);
+    cudaError_t e = launch_project(c->v, psi, prec, c->f64_mode, nbands, sk, ss, sn, c->variant[prec == DFTU_C64 ? 1 : 0], st,
+                                   c->gauge_on);
     if (e != cudaSuccess) return cuda_fail(c, e, "project");
     c->last_stream = st;
     c->proj_ready = true;
@@ -607,7 +615,8 @@ dftu_status dftu_apply(dftu_handle h, void* psi_out, dftu_prec prec, int nbands,
     strides(c, nbands, ld_band, sk, ss, sn);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = launch_apply(c->v, psi_out, prec, c->f64_mode, nbands, sk, ss, sn, coef ? coef : c->d_coef_one,
-                                 c->d_color_order, c->color_beg, c->variant[prec == DFTU_C64 ? 3 : 2], accumulate ? 1 : 0, st);
+                                 c->d_color_order, c->color_beg, c->variant[prec == DFTU_C64 ? 3 : 2], accumulate ? 1 : 0, st,
+                                 c->gauge_on);
     if (e != cudaSuccess) return cuda_fail(c, e, "apply");
     c->last_stream = st;
     return DFTU_OK;
@@ -629,7 +638,8 @@ dftu_status dftu_taylor_step(dftu_handle h, void* psi, void* work, dftu_prec pre
     strides(c, nbands, ld_band, sk, ss, sn);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int vp = c->variant[prec == DFTU_C64 ? 1 : 0], va = c->variant[prec == DFTU_C64 ? 3 : 2];
-    cudaError_t e = launch_project(c->v, psi, prec, c->f64_mode, nbands, sk, ss, sn, vp, st);
+    const bool G = c->gauge_on;
+    cudaError_t e = launch_project(c->v, psi, prec, c->f64_mode, nbands, sk, ss, sn, vp, st, G);
     if (e == cudaSuccess) e = launch_nbar(c->v, nbands, st);
     if (e == cudaSuccess) e = launch_occupations(c->v, f, nbands, st);
     if (e == cudaSuccess) e = launch_acbn0(c->v, st);
@@ -637,10 +647,10 @@ dftu_status dftu_taylor_step(dftu_handle h, void* psi, void* work, dftu_prec pre
     for (int j = 1; j <= order && e == cudaSuccess; ++j) {
         const double* cj = c->d_taylor + 2 * (j - 1);
         // term_j = (-i dt / j) V_U term_{j-1}, from the projections of term_{j-1} held by the handle
-        e = launch_apply(c->v, work, prec, c->f64_mode, nbands, sk, ss, sn, cj, c->d_color_order, c->color_beg, va, 0, st);
+        e = launch_apply(c->v, work, prec, c->f64_mode, nbands, sk, ss, sn, cj, c->d_color_order, c->color_beg, va, 0, st, G);
         if (e == cudaSuccess)
-            e = launch_apply(c->v, psi, prec, c->f64_mode, nbands, sk, ss, sn, cj, c->d_color_order, c->color_beg, va, 1, st);
-        if (e == cudaSuccess && j < order) e = launch_project(c->v, work, prec, c->f64_mode, nbands, sk, ss, sn, vp, st);
+            e = launch_apply(c->v, psi, prec, c->f64_mode, nbands, sk, ss, sn, cj, c->d_color_order, c->color_beg, va, 1, st, G);
+        if (e == cudaSuccess && j < order) e = launch_project(c->v, work, prec, c->f64_mode, nbands, sk, ss, sn, vp, st, G);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "taylor_step");
     c->last_stream = st;
@@ -654,6 +664,7 @@ dftu_status dftu_forces(dftu_handle h, const void* const* dpsi, dftu_prec prec, 
     Ctx* c = reinterpret_cast<Ctx*>(h);
     if (!c) return DFTU_ERR_INVALID_ARG;
     if (!c->pot_ready || !c->proj_ready) return fail(c, DFTU_ERR_NOT_READY, "forces: call dftu_project, dftu_occupations and dftu_acbn0_uj first");
+    if (c->gauge_on) return fail(c, DFTU_ERR_INVALID_ARG, "forces: not defined with a vector potential set (dftu_set_vector_potential with NULL clears it)");
     if (!dpsi || !dpsi[0] || !dpsi[1] || !dpsi[2] || !f || !F_out || (prec != DFTU_C128 && prec != DFTU_C64) ||
         !valid_stride_args(c, nbands, ld_band) || nbands != c->proj_nbands)
         return fail(c, DFTU_ERR_INVALID_ARG, "forces: null pointers, bad precision, ld_band < npts or nbands differs from the projected states");
@@ -672,6 +683,66 @@ dftu_status dftu_forces(dftu_handle h, const void* const* dpsi, dftu_prec prec, 
     if (e == cudaSuccess) e = cudaMemcpyAsync(F_out, c->d_forces, 3 * c->atoms.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(c, e, "forces");
+    c->last_stream = st;
+    return DFTU_OK;
+}
+
+dftu_status dftu_set_vector_potential(dftu_handle h, const double* A, dftu_stream stream) {
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c) return DFTU_ERR_INVALID_ARG;
+    if (!c->atoms_ready) return fail(c, DFTU_ERR_NOT_READY, "set_vector_potential: call dftu_setup_atoms first");
+    if (c->spin == DFTU_NONCOLLINEAR && A)
+        return fail(c, DFTU_ERR_INVALID_ARG, "set_vector_potential: the gauge-invariant operator is built for collinear and unpolarised states");
+    if (!A) {
+        c->gauge_on = false;
+        return DFTU_OK;
+    }
+    Guard g(c->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_gauge_phases(c->v, A, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set_vector_potential");
+    c->gauge_on = true;
+    c->proj_ready = c->occ_ready = c->pot_ready = false;   // earlier projections used the previous phases
+    c->last_stream = st;
+    return DFTU_OK;
+}
+
+dftu_status dftu_hubbard_current(dftu_handle h, const void* psi, dftu_prec prec, int nbands, int64_t ld_band, const double* f,
+                                 double* J_out, double* J_atom_out, dftu_stream stream) {
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c) return DFTU_ERR_INVALID_ARG;
+    if (!c->pot_ready || !c->proj_ready)
+        return fail(c, DFTU_ERR_NOT_READY, "hubbard_current: call dftu_project, dftu_occupations and dftu_acbn0_uj first");
+    if (c->spin == DFTU_NONCOLLINEAR) return fail(c, DFTU_ERR_INVALID_ARG, "hubbard_current: collinear and unpolarised states only");
+    if (!psi || !f || (!J_out && !J_atom_out) || (prec != DFTU_C128 && prec != DFTU_C64) || !valid_stride_args(c, nbands, ld_band) ||
+        nbands != c->proj_nbands)
+        return fail(c, DFTU_ERR_INVALID_ARG, "hubbard_current: null pointers, bad precision, ld_band < npts or nbands differs from the projected states");
+    Guard g(c->device);
+    int64_t sk, ss, sn;
+    strides(c, nbands, ld_band, sk, ss, sn);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t gstride = (int64_t)c->nk * c->ns * c->max_bands * c->MT;
+    cudaError_t e = cudaSuccess;
+    for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+        View vq = c->v;   // the same states projected onto phi_m d_a, into the gradient buffer
+        vq.phi64 = c->v.phid64 + a * c->phi_total;
+        vq.phi_hi = c->v.phid_hi + a * c->phi_total;
+        vq.phi_lo = c->v.phid_lo + a * c->phi_total;
+        vq.p = c->v.pgrad + a * gstride;
+        e = launch_project(vq, psi, prec, c->f64_mode, nbands, sk, ss, sn, c->variant[prec == DFTU_C64 ? 1 : 0], st, c->gauge_on);
+    }
+    if (e == cudaSuccess) e = launch_current(c->v, f, nbands, c->d_current, st);
+    const int na = (int)c->atoms.size();
+    std::vector<double> Jat(3 * (size_t)na);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Jat.data(), c->d_current, Jat.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "hubbard_current");
+    if (J_atom_out) std::copy(Jat.begin(), Jat.end(), J_atom_out);
+    if (J_out) {
+        J_out[0] = J_out[1] = J_out[2] = 0.0;
+        for (int a = 0; a < na; ++a)
+            for (int d = 0; d < 3; ++d) J_out[d] += Jat[3 * a + d];
+    }
     c->last_stream = st;
     return DFTU_OK;
 }

@@ -78,13 +78,37 @@ __device__ __forceinline__ double pair_to_double(float h, float l, int sc) {
     return __longlong_as_double((long long)D);
 }
 
+// (bh + bl) * (g.x + g.z + i (g.y + g.w)) componentwise as a new float pair (exact hi products, TwoSum,
+// cross terms with the low parts in the low word), renormalised with TwoSum so that |lo| <= ulp(hi)/2.
+__device__ __forceinline__ void rot_pair_norm(float2& bh, float2& bl, float4 g) {
+    const float2 uh = make_float2(g.x, g.y), wh = make_float2(-g.y, g.x);
+    const float2 ul = make_float2(g.z, g.w), wl = make_float2(-g.w, g.z);
+    const float2 xr = make_float2(bh.x, bh.x), xi = make_float2(bh.y, bh.y);
+    const float2 P = __fmul2_rn(uh, xr), R = __fmul2_rn(wh, xi);
+    const float2 eP = __ffma2_rn(uh, xr, make_float2(-P.x, -P.y));
+    const float2 eR = __ffma2_rn(wh, xi, make_float2(-R.x, -R.y));
+    float2 s = __fadd2_rn(P, R);
+    float2 bb = __fadd2_rn(s, make_float2(-P.x, -P.y));
+    float2 t = __fadd2_rn(__fadd2_rn(P, make_float2(bb.x - s.x, bb.y - s.y)), __fadd2_rn(R, make_float2(-bb.x, -bb.y)));
+    float2 lo = __fadd2_rn(__fadd2_rn(eP, eR), t);
+    lo = __ffma2_rn(uh, make_float2(bl.x, bl.x), lo);
+    lo = __ffma2_rn(ul, xr, lo);
+    lo = __ffma2_rn(wh, make_float2(bl.y, bl.y), lo);
+    lo = __ffma2_rn(wl, xi, lo);
+    const float2 h = __fadd2_rn(s, lo);   // TwoSum(s, lo)
+    bb = __fadd2_rn(h, make_float2(-s.x, -s.y));
+    bl = __fadd2_rn(__fadd2_rn(s, make_float2(bb.x - h.x, bb.y - h.y)), __fadd2_rn(lo, make_float2(-bb.x, -bb.y)));
+    bh = h;
+}
+
 // Each lane handles U points of its band at a time: U loads in flight, then the arithmetic, then U
 // stores (the points of one tile are distinct grid points, so the batch never aliases).  Orbital rows
 // up to Q*U past the tile are staged as zeros, so the arithmetic needs no bounds test.
-template <int POL, int Q, int M, int U, int PF>
+// With G, the update of point j is multiplied by exp(-i A.d_j) (the gauge phase table in s_gauge).
+template <int POL, int Q, int M, int U, int PF, int G>
 __device__ __forceinline__ void apply_body(const Tile& t, const ApplyArgs& a, int64_t off, int q, int bl, const int* s_idx,
                                            const unsigned char* s_first, const unsigned char* after_idx,
-                                           const unsigned char* after_c, int pe) {
+                                           const unsigned char* after_c, int pe, const unsigned char* s_gauge) {
     if (POL == A_F64) {
         double2* row = reinterpret_cast<double2*>(a.psi) + off;
         const double* s_phi = reinterpret_cast<const double*>(after_c);
@@ -109,10 +133,22 @@ __device__ __forceinline__ void apply_body(const Tile& t, const ApplyArgs& a, in
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const double* ph = s_phi + (i0 + u * Q) * M;
+                if (G) {
+                    double2 d = make_double2(0.0, 0.0);
 #pragma unroll
-                for (int m = 0; m < M; ++m) {
-                    x[u].x = fma(ph[m], cc[m].x, x[u].x);
-                    x[u].y = fma(ph[m], cc[m].y, x[u].y);
+                    for (int m = 0; m < M; ++m) {
+                        d.x = fma(ph[m], cc[m].x, d.x);
+                        d.y = fma(ph[m], cc[m].y, d.y);
+                    }
+                    const double2 g = reinterpret_cast<const double2*>(s_gauge)[i0 + u * Q];   // x += conj(g) d
+                    x[u].x += fma(g.x, d.x, g.y * d.y);
+                    x[u].y += fma(g.x, d.y, -g.y * d.x);
+                } else {
+#pragma unroll
+                    for (int m = 0; m < M; ++m) {
+                        x[u].x = fma(ph[m], cc[m].x, x[u].x);
+                        x[u].y = fma(ph[m], cc[m].y, x[u].y);
+                    }
                 }
             }
 #pragma unroll
@@ -141,6 +177,7 @@ __device__ __forceinline__ void apply_body(const Tile& t, const ApplyArgs& a, in
         for (int m = 0; m < M; ++m)
             ce = max(ce, max((__float_as_int(ch[m].x) >> 23) & 0xFF, (__float_as_int(ch[m].y) >> 23) & 0xFF) - 126);
         const int ebound = min(max(pe + ce, -120), 120);          // |phi_hi c_hi| < 2^ebound
+        // (the gauge rotation acts on the finished sum, so the accumulator bound is unchanged)
         const float Cv = pow2f(ebound + 5);
         const float2 C2 = make_float2(Cv, Cv), mone = make_float2(-1.f, -1.f);
         for (int i0 = q; i0 < t.np; i0 += Q * U) {
@@ -176,6 +213,10 @@ __device__ __forceinline__ void apply_body(const Tile& t, const ApplyArgs& a, in
                 float2 dh = __fadd2_rn(acc, make_float2(-Cv, -Cv));          // exact
                 float2 hh = __fadd2_rn(dh, lo);                               // Fast2Sum: |lo| << |dh| or dh = 0
                 float2 ll = __fadd2_rn(lo, make_float2(-(hh.x - dh.x), -(hh.y - dh.y)));
+                if (G) {
+                    const float4 g = reinterpret_cast<const float4*>(s_gauge)[i0 + u * Q];
+                    rot_pair_norm(hh, ll, make_float4(g.x, -g.y, g.z, -g.w));   // times conj(g)
+                }
                 x[u].x += pair_to_double(hh.x, ll.x, 0);
                 x[u].y += pair_to_double(hh.y, ll.y, 0);
             }
@@ -209,10 +250,22 @@ __device__ __forceinline__ void apply_body(const Tile& t, const ApplyArgs& a, in
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const float4* ph = s_phi + (i0 + u * Q) * M;
+                if (G) {
+                    float2 d = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int m = 0; m < M; ++m) {
-                    float4 f = ph[m];
-                    x[u] = __ffma2_rn(make_float2(f.x, f.y), cc[m], x[u]);
+                    for (int m = 0; m < M; ++m) {
+                        float4 f = ph[m];
+                        d = __ffma2_rn(make_float2(f.x, f.y), cc[m], d);
+                    }
+                    const float4 g = reinterpret_cast<const float4*>(s_gauge)[i0 + u * Q];   // x += conj(g) d
+                    x[u] = __ffma2_rn(make_float2(g.x, -g.y), make_float2(d.x, d.x), x[u]);
+                    x[u] = __ffma2_rn(make_float2(g.y, g.x), make_float2(d.y, d.y), x[u]);
+                } else {
+#pragma unroll
+                    for (int m = 0; m < M; ++m) {
+                        float4 f = ph[m];
+                        x[u] = __ffma2_rn(make_float2(f.x, f.y), cc[m], x[u]);
+                    }
                 }
             }
 #pragma unroll
@@ -225,7 +278,7 @@ __device__ __forceinline__ void apply_body(const Tile& t, const ApplyArgs& a, in
 }
 
 // One work item: tile `tile_id` (a tile of the current colour) of the system (v, a), component ks, band chunk `chunk`.
-template <int POL, int Q, int NBG, int U, int PF>
+template <int POL, int Q, int NBG, int U, int PF, int G>
 __device__ __forceinline__ void apply_item(const View& v, const ApplyArgs& a, int tile_id, int ks, int chunk,
                                            unsigned char* smem, int& s_pe, unsigned char* s_first) {
     static_assert(Q * U <= TILE_PAD - TILE, "batched loops read up to Q*U rows past the tile");
@@ -260,6 +313,16 @@ __device__ __forceinline__ void apply_item(const View& v, const ApplyArgs& a, in
         }
         if (POL == A_PAIR) atomicMax(&s_pe, pe);
     }
+    // gauge phases of the tile's points (zeros past the tile), after the orbital rows of the largest shell
+    unsigned char* s_gauge = after_c + (size_t)TILE_PAD * v.maxM * (POL == A_F64 ? sizeof(double) : sizeof(float4));
+    if (G) {
+        if (POL == A_F64)
+            for (int i = threadIdx.x; i < TILE_PAD; i += CTA)
+                reinterpret_cast<double2*>(s_gauge)[i] = (i < t.np) ? v.gauge_d[t.p0 + i] : make_double2(0.0, 0.0);
+        else
+            for (int i = threadIdx.x; i < TILE_PAD; i += CTA)
+                reinterpret_cast<float4*>(s_gauge)[i] = (i < t.np) ? v.gauge_f[t.p0 + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     const int lane = threadIdx.x & 31;
     const int bl = (threadIdx.x >> 5) * BPW + lane / Q;
     const int q = lane & (Q - 1);
@@ -269,8 +332,8 @@ __device__ __forceinline__ void apply_item(const View& v, const ApplyArgs& a, in
         const int band0 = (chunk * NBG + g) * BPC;
         if (band0 >= a.nbands) break;
         __syncthreads();   // staging done / previous group's readers done with the coefficient table
-        if (threadIdx.x < BPC * M) {
-            int cb = threadIdx.x / M, m = threadIdx.x % M;
+        for (int e = threadIdx.x; e < BPC * M; e += CTA) {   // BPC * M exceeds CTA when Q = 4 and M >= 5
+            int cb = e / M, m = e % M;
             int band = band0 + cb;
             double2 c = make_double2(0.0, 0.0);
             if (band < a.nbands) {
@@ -314,21 +377,21 @@ __device__ __forceinline__ void apply_item(const View& v, const ApplyArgs& a, in
             const int64_t off = (int64_t)k * a.sk + (int64_t)s * a.ss + (int64_t)band * a.sn;
             const int pe = s_pe;
             switch (M) {
-                case 1: apply_body<POL, Q, 1, U, PF>(t, a, off, q, bl, s_idx, s_first, after_idx, after_c, pe); break;
-                case 3: apply_body<POL, Q, 3, U, PF>(t, a, off, q, bl, s_idx, s_first, after_idx, after_c, pe); break;
-                case 5: apply_body<POL, Q, 5, U, PF>(t, a, off, q, bl, s_idx, s_first, after_idx, after_c, pe); break;
-                default: apply_body<POL, Q, 7, U, PF>(t, a, off, q, bl, s_idx, s_first, after_idx, after_c, pe); break;
+                case 1: apply_body<POL, Q, 1, U, PF, G>(t, a, off, q, bl, s_idx, s_first, after_idx, after_c, pe, s_gauge); break;
+                case 3: apply_body<POL, Q, 3, U, PF, G>(t, a, off, q, bl, s_idx, s_first, after_idx, after_c, pe, s_gauge); break;
+                case 5: apply_body<POL, Q, 5, U, PF, G>(t, a, off, q, bl, s_idx, s_first, after_idx, after_c, pe, s_gauge); break;
+                default: apply_body<POL, Q, 7, U, PF, G>(t, a, off, q, bl, s_idx, s_first, after_idx, after_c, pe, s_gauge); break;
             }
         }
     }
 }
 
-template <int POL, int Q, int NBG, int U, int PF>
+template <int POL, int Q, int NBG, int U, int PF, int G>
 __global__ void __launch_bounds__(CTA, 3) k_apply(View v, ApplyArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_pe;
     __shared__ unsigned char s_first[TILE];
-    apply_item<POL, Q, NBG, U, PF>(v, a, a.tile_list[blockIdx.x], blockIdx.z, blockIdx.y, smem, s_pe, s_first);
+    apply_item<POL, Q, NBG, U, PF, G>(v, a, a.tile_list[blockIdx.x], blockIdx.z, blockIdx.y, smem, s_pe, s_first);
 }
 
 // Persistent form over many systems: (system, tile, k*spin) items of one colour from a counter.
@@ -351,27 +414,28 @@ __global__ void __launch_bounds__(CTA, 3) k_apply_batch(const View* __restrict__
         ApplyArgs a{const_cast<void*>(pa.psi), pa.sk, pa.ss, pa.sn, pa.nbands, coef, nullptr, accumulate};
         const int nchunks = (pa.nbands + BPC * NBG - 1) / (BPC * NBG);
         for (int c = 0; c < nchunks; ++c) {
-            apply_item<POL, Q, NBG, U, PF>(v, a, w.y, w.z, c, smem, s_pe, s_first);
+            apply_item<POL, Q, NBG, U, PF, 0>(v, a, w.y, w.z, c, smem, s_pe, s_first);
             __syncthreads();
         }
     }
 }
 
-template <int POL, int Q, int NBG, int U, int PF>
+template <int POL, int Q, int NBG, int U, int PF, int G = 0>
 static cudaError_t run_apply(const View& v, ApplyArgs a, const int* color_order, const std::vector<int>& color_beg,
                              cudaStream_t st) {
     constexpr int BPC = (CTA / 32) * (32 / Q);
-    size_t smem = TILE * sizeof(int) + BPC * MAXM * 16 + (size_t)TILE_PAD * v.maxM * (POL == A_F64 ? sizeof(double) : sizeof(float4));
+    size_t smem = TILE * sizeof(int) + BPC * MAXM * 16 + (size_t)TILE_PAD * v.maxM * (POL == A_F64 ? sizeof(double) : sizeof(float4)) +
+                  (G ? (size_t)TILE_PAD * 16 : 0);
+    auto fn = k_apply<POL, Q, NBG, U, PF, G>;
     cudaError_t e = cudaSuccess;
-    if (!smem_configured((const void*)k_apply<POL, Q, NBG, U, PF>, (int)smem))
-        e = cudaFuncSetAttribute(k_apply<POL, Q, NBG, U, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (!smem_configured((const void*)fn, (int)smem)) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     for (size_t c = 0; c + 1 < color_beg.size(); ++c) {
         int n = color_beg[c + 1] - color_beg[c];
         if (n == 0) continue;
         a.tile_list = color_order + color_beg[c];
         dim3 grid(n, (a.nbands + BPC * NBG - 1) / (BPC * NBG), v.nk * v.ns);
-        k_apply<POL, Q, NBG, U, PF><<<grid, CTA, smem, st>>>(v, a);
+        fn<<<grid, CTA, smem, st>>>(v, a);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -380,8 +444,13 @@ static cudaError_t run_apply(const View& v, ApplyArgs a, const int* color_order,
 
 cudaError_t launch_apply(const View& v, void* psi, dftu_prec prec, dftu_f64_mode mode, int nbands,
                          int64_t sk, int64_t ss, int64_t sn, const double* coef, const int* color_order,
-                         const std::vector<int>& color_beg, int variant, int accumulate, cudaStream_t st) {
+                         const std::vector<int>& color_beg, int variant, int accumulate, cudaStream_t st, bool gauge) {
     ApplyArgs a{psi, sk, ss, sn, nbands, coef, nullptr, accumulate};
+    if (gauge) {   // one shape per arithmetic policy with the gauge phases (Sec. V)
+        if (prec == DFTU_C64) return run_apply<A_F32, 8, 4, 8, 0, 1>(v, a, color_order, color_beg, st);
+        if (mode == DFTU_F64_NATIVE) return run_apply<A_F64, 8, 4, 4, 0, 1>(v, a, color_order, color_beg, st);
+        return run_apply<A_PAIR, 8, 4, 4, 0, 1>(v, a, color_order, color_beg, st);
+    }
     if (prec == DFTU_C64) {
         switch (variant) {   // (lanes per band, band groups per CTA, points in flight per lane)
             case 1: return run_apply<A_F32, 8, 4, 4, 0>(v, a, color_order, color_beg, st);

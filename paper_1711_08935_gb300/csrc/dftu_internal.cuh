@@ -65,6 +65,11 @@ struct View {
     const int* pt_idx;     // [S] wrapped linear index, GPU order
     const int* pt_u;       // [S][3] unfolded integer coordinates, GPU order
     const unsigned char* pt_first;   // [S] 1 if no tile of an earlier apply colour covers this grid point
+    double2* gauge_d;      // [S] (cos, sin) of A.d_j, d_j = point minus atom centre (Sec. V, Eq. 16)
+    float4* gauge_f;       // [S] the same as FP32 pairs (cos_hi, sin_hi, cos_lo, sin_lo)
+    double* phid64;        // [3][sum S_I M_I] orbitals times the displacement component d_a (Eq. 17)
+    float* phid_hi;        // [3][sum S_I M_I] FP32 split of phid64
+    float* phid_lo;
     double* phi64;         // [sum S_I M_I]
     float* phi_hi;
     float* phi_lo;
@@ -100,6 +105,7 @@ struct Ctx {
     bool atoms_ready = false, proj_ready = false, occ_ready = false, pot_ready = false;
     int proj_nbands = 0;
     int variant[4] = {0, 0, 0, 0};   // project c128, project c64, apply c128, apply c64
+    bool gauge_on = false;           // dftu_set_vector_potential with a non-null A
     cudaStream_t last_stream = nullptr;
     std::string err;
 
@@ -121,6 +127,7 @@ struct Ctx {
     double* d_coef_one = nullptr;
     double* d_taylor = nullptr;      // [MAX_TAYLOR] complex Taylor coefficients -i dt / j
     double* d_forces = nullptr;      // [natoms][3]
+    double* d_current = nullptr;     // [natoms][3] per-atom Hubbard current
     std::vector<int> h_coul_set;     // host copies, so hot-path calls never read the device
     std::vector<double> h_fixU;
 };
@@ -161,13 +168,17 @@ cudaError_t launch_lowdin(const View& v, double* work_S, cudaStream_t st);
 
 constexpr int NVARIANTS = 8;   // shapes per streaming kernel (see dftu_set_kernel_variant)
 cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_f64_mode mode, int nbands,
-                           int64_t sk, int64_t ss, int64_t sn, int variant, cudaStream_t st);
+                           int64_t sk, int64_t ss, int64_t sn, int variant, cudaStream_t st, bool gauge = false);
 cudaError_t launch_nbar(const View& v, int nbands, cudaStream_t st);
 cudaError_t launch_occupations(const View& v, const double* f, int nbands, cudaStream_t st);
 cudaError_t launch_acbn0(const View& v, cudaStream_t st);
 cudaError_t launch_apply(const View& v, void* psi, dftu_prec prec, dftu_f64_mode mode, int nbands,
                          int64_t sk, int64_t ss, int64_t sn, const double* coef, const int* color_order,
-                         const std::vector<int>& color_beg, int variant, int accumulate, cudaStream_t st);
+                         const std::vector<int>& color_beg, int variant, int accumulate, cudaStream_t st,
+                         bool gauge = false);
+cudaError_t launch_gauge_phases(const View& v, const double* A, cudaStream_t st);
+cudaError_t launch_displaced_orbitals(const View& v, int64_t phi_total, cudaStream_t st);
+cudaError_t launch_current(const View& v, const double* f, int nbands, double* Jat, cudaStream_t st);
 cudaError_t launch_taylor_coefs(double dt, int order, double* coefs, cudaStream_t st);
 cudaError_t launch_forces(const View& v, const double* f, int nbands, double* F, cudaStream_t st);
 cudaError_t launch_project_batch(const BatchLaunch& b, dftu_prec prec, dftu_f64_mode mode, int variant, cudaStream_t st);

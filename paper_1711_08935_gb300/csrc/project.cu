@@ -65,9 +65,14 @@ __device__ __forceinline__ void write_partial(const View& v, const Tile& t, int 
 // ------------------------------------------------------------------------------------------------
 // F64 policy
 // ------------------------------------------------------------------------------------------------
-template <int M, int Q>
+// x * (g.x + i g.y)
+__device__ __forceinline__ double2 crot(double2 x, double2 g) {
+    return make_double2(fma(g.x, x.x, -g.y * x.y), fma(g.y, x.x, g.x * x.y));
+}
+
+template <int M, int Q, int G>
 __device__ __forceinline__ void proj_body_f64(const View& v, const Tile& t, int ks, int band, const double2* __restrict__ row,
-                                              const int* s_idx, const double* s_phi) {
+                                              const int* s_idx, const double* s_phi, const double2* s_g) {
     const int q = threadIdx.x & (Q - 1);
     double2 acc[M];
 #pragma unroll
@@ -78,6 +83,9 @@ __device__ __forceinline__ void proj_body_f64(const View& v, const Tile& t, int 
             double2 x[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) x[u] = __ldg(row + s_idx[i + u * Q]);
+            if (G)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) x[u] = crot(x[u], s_g[i + u * Q]);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const double* ph = s_phi + (i + u * Q) * M;
@@ -90,6 +98,7 @@ __device__ __forceinline__ void proj_body_f64(const View& v, const Tile& t, int 
         }
         for (; i < t.np; i += Q) {
             double2 x = __ldg(row + s_idx[i]);
+            if (G) x = crot(x, s_g[i]);
             const double* ph = s_phi + i * M;
 #pragma unroll
             for (int m = 0; m < M; ++m) {
@@ -112,9 +121,9 @@ __device__ __forceinline__ void proj_body_f64(const View& v, const Tile& t, int 
 // ------------------------------------------------------------------------------------------------
 // F32 policy (complex64 states)
 // ------------------------------------------------------------------------------------------------
-template <int M, int Q, int CH, int PF>
+template <int M, int Q, int CH, int PF, int G>
 __device__ __forceinline__ void proj_body_f32(const View& v, const Tile& t, int ks, int band, const float2* __restrict__ row,
-                                              const int* s_idx, const float4* s_phi) {
+                                              const int* s_idx, const float4* s_phi, const float4* s_g) {
     const int q = threadIdx.x & (Q - 1);
     DF2 R[M];
 #pragma unroll
@@ -127,6 +136,13 @@ __device__ __forceinline__ void proj_body_f32(const View& v, const Tile& t, int 
                 int i = i0 + c * Q;
                 x[c] = (i < t.np) ? __ldg(row + s_idx[i]) : make_float2(0.f, 0.f);
             }
+            if (G)
+#pragma unroll
+                for (int c = 0; c < CH; ++c) {   // x * (cos + i sin) in FP32 (rows past the tile hold zeros)
+                    const float4 g = s_g[i0 + c * Q];
+                    x[c] = ffma2(make_float2(-g.y, g.x), make_float2(x[c].y, x[c].y),
+                                 __fmul2_rn(make_float2(g.x, g.y), make_float2(x[c].x, x[c].x)));
+                }
             if (PF) {
 #pragma unroll
                 for (int c = 0; c < CH; ++c) {
@@ -187,9 +203,32 @@ __device__ __forceinline__ void split_scaled(double x, int Em, float& hi, float&
 
 __device__ __forceinline__ int exp_field(double x) { return (__double2hiint(x) >> 20) & 0x7FF; }
 
-template <int M, int Q, int CH, int PF>
+// (bh + bl) * (g.x + g.z + i (g.y + g.w)) as a new float pair, componentwise for (re, im): the hi
+// products are formed exactly (product + FMA residual) and added with TwoSum, the cross terms with
+// the low parts go into the low word.  Error ~2^-47 of |b|; the modulus grows by at most sqrt(2) per
+// component.
+__device__ __forceinline__ void rot_pair(float2& bh, float2& bl, float4 g) {
+    const float2 uh = make_float2(g.x, g.y), wh = make_float2(-g.y, g.x);
+    const float2 ul = make_float2(g.z, g.w), wl = make_float2(-g.w, g.z);
+    const float2 xr = make_float2(bh.x, bh.x), xi = make_float2(bh.y, bh.y);
+    const float2 P = __fmul2_rn(uh, xr), R = __fmul2_rn(wh, xi);
+    const float2 eP = ffma2(uh, xr, make_float2(-P.x, -P.y));
+    const float2 eR = ffma2(wh, xi, make_float2(-R.x, -R.y));
+    const float2 s = fadd2(P, R);
+    const float2 bb = fadd2(s, make_float2(-P.x, -P.y));
+    const float2 t = fadd2(fadd2(P, make_float2(bb.x - s.x, bb.y - s.y)), fadd2(R, make_float2(-bb.x, -bb.y)));
+    float2 lo = fadd2(fadd2(eP, eR), t);
+    lo = ffma2(uh, make_float2(bl.x, bl.x), lo);
+    lo = ffma2(ul, xr, lo);
+    lo = ffma2(wh, make_float2(bl.y, bl.y), lo);
+    lo = ffma2(wl, xi, lo);
+    bh = s;
+    bl = lo;
+}
+
+template <int M, int Q, int CH, int PF, int G>
 __device__ __forceinline__ void proj_body_pair(const View& v, const Tile& t, int ks, int band, const double2* __restrict__ row,
-                                               const int* s_idx, const float4* s_phi, int pe) {
+                                               const int* s_idx, const float4* s_phi, int pe, const float4* s_g) {
     const int q = threadIdx.x & (Q - 1);
     DF2 R[M];
 #pragma unroll
@@ -197,8 +236,9 @@ __device__ __forceinline__ void proj_body_pair(const View& v, const Tile& t, int
     int Em_run = 0;
     bool bad = false;
     // chain offset C = 2^(pe + 1 + log2 CH + 2) >= 4 * CH * max|phi x'|, |x'| < 2, |phi| < 2^pe
+    // (one more power of two when x' is rotated by a gauge phase: |x'| < 2 sqrt 2)
     constexpr int LOG2CH = (CH >= 16) ? 4 : (CH >= 8) ? 3 : (CH >= 4) ? 2 : (CH >= 2) ? 1 : 0;
-    const float Cv = pow2f(min(max(pe + 3 + LOG2CH, -100), 100));
+    const float Cv = pow2f(min(max(pe + 3 + G + LOG2CH, -100), 100));
     const float2 C2 = make_float2(Cv, Cv);
     const float2 mone = make_float2(-1.f, -1.f);
     if (row) {
@@ -241,6 +281,7 @@ __device__ __forceinline__ void proj_body_pair(const View& v, const Tile& t, int
                 float2 bh, bl;
                 split_scaled(x[c].x, Em_run, bh.x, bl.x);
                 split_scaled(x[c].y, Em_run, bh.y, bl.y);
+                if (G) rot_pair(bh, bl, s_g[i0 + c * Q]);
                 const float4* ph = s_phi + (i0 + c * Q) * M;
 #pragma unroll
                 for (int m = 0; m < M; ++m) {
@@ -302,7 +343,7 @@ enum Pol { P_F64 = 0, P_PAIR = 1, P_F32 = 2 };
 
 // One work item: tile `tile_id` of the system described by (v, a), spin/component index ks, every band of
 // band chunk `chunk` (NBG groups of BPC bands).  The tile is staged in shared memory once.
-template <int POL, int Q, int CH, int NBG, int PF>
+template <int POL, int Q, int CH, int NBG, int PF, int G>
 __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, int tile_id, int ks, int chunk,
                                              unsigned char* smem, int* s_pe) {
     int* s_idx = reinterpret_cast<int*>(smem);
@@ -330,6 +371,16 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
         }
         if (POL == P_PAIR) atomicMax(s_pe, pe);
     }
+    // gauge phases of the tile's points (zeros past the tile), after the orbital rows of the largest shell
+    unsigned char* s_gauge = smem + TILE * sizeof(int) + (size_t)TILE_PAD * v.maxM * (POL == P_F64 ? sizeof(double) : sizeof(float4));
+    if (G) {
+        if (POL == P_F64)
+            for (int i = threadIdx.x; i < TILE_PAD; i += CTA)
+                reinterpret_cast<double2*>(s_gauge)[i] = (i < t.np) ? v.gauge_d[t.p0 + i] : make_double2(0.0, 0.0);
+        else
+            for (int i = threadIdx.x; i < TILE_PAD; i += CTA)
+                reinterpret_cast<float4*>(s_gauge)[i] = (i < t.np) ? v.gauge_f[t.p0 + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     __syncthreads();
 
     // ---- stream NBG groups of BPC bands over the staged tile
@@ -342,40 +393,43 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
         if (POL == P_F64) {
             const double* s_phi = reinterpret_cast<const double*>(smem + TILE * sizeof(int));
             const double2* row = active ? reinterpret_cast<const double2*>(a.psi) + off : nullptr;
+            const double2* s_g = reinterpret_cast<const double2*>(s_gauge);
             switch (t.M) {
-                case 1: proj_body_f64<1, Q>(v, t, ks, band, row, s_idx, s_phi); break;
-                case 3: proj_body_f64<3, Q>(v, t, ks, band, row, s_idx, s_phi); break;
-                case 5: proj_body_f64<5, Q>(v, t, ks, band, row, s_idx, s_phi); break;
-                default: proj_body_f64<7, Q>(v, t, ks, band, row, s_idx, s_phi); break;
+                case 1: proj_body_f64<1, Q, G>(v, t, ks, band, row, s_idx, s_phi, s_g); break;
+                case 3: proj_body_f64<3, Q, G>(v, t, ks, band, row, s_idx, s_phi, s_g); break;
+                case 5: proj_body_f64<5, Q, G>(v, t, ks, band, row, s_idx, s_phi, s_g); break;
+                default: proj_body_f64<7, Q, G>(v, t, ks, band, row, s_idx, s_phi, s_g); break;
             }
         } else if (POL == P_PAIR) {
             const float4* s_phi = reinterpret_cast<const float4*>(smem + TILE * sizeof(int));
             const double2* row = active ? reinterpret_cast<const double2*>(a.psi) + off : nullptr;
             const int pe = *s_pe;
+            const float4* s_g = reinterpret_cast<const float4*>(s_gauge);
             switch (t.M) {
-                case 1: proj_body_pair<1, Q, CH, PF>(v, t, ks, band, row, s_idx, s_phi, pe); break;
-                case 3: proj_body_pair<3, Q, CH, PF>(v, t, ks, band, row, s_idx, s_phi, pe); break;
-                case 5: proj_body_pair<5, Q, CH, PF>(v, t, ks, band, row, s_idx, s_phi, pe); break;
-                default: proj_body_pair<7, Q, CH, PF>(v, t, ks, band, row, s_idx, s_phi, pe); break;
+                case 1: proj_body_pair<1, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phi, pe, s_g); break;
+                case 3: proj_body_pair<3, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phi, pe, s_g); break;
+                case 5: proj_body_pair<5, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phi, pe, s_g); break;
+                default: proj_body_pair<7, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phi, pe, s_g); break;
             }
         } else {
             const float4* s_phi = reinterpret_cast<const float4*>(smem + TILE * sizeof(int));
             const float2* row = active ? reinterpret_cast<const float2*>(a.psi) + off : nullptr;
+            const float4* s_g = reinterpret_cast<const float4*>(s_gauge);
             switch (t.M) {
-                case 1: proj_body_f32<1, Q, CH, PF>(v, t, ks, band, row, s_idx, s_phi); break;
-                case 3: proj_body_f32<3, Q, CH, PF>(v, t, ks, band, row, s_idx, s_phi); break;
-                case 5: proj_body_f32<5, Q, CH, PF>(v, t, ks, band, row, s_idx, s_phi); break;
-                default: proj_body_f32<7, Q, CH, PF>(v, t, ks, band, row, s_idx, s_phi); break;
+                case 1: proj_body_f32<1, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phi, s_g); break;
+                case 3: proj_body_f32<3, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phi, s_g); break;
+                case 5: proj_body_f32<5, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phi, s_g); break;
+                default: proj_body_f32<7, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phi, s_g); break;
             }
         }
     }
 }
 
-template <int POL, int Q, int CH, int NBG, int PF, int MINB>
+template <int POL, int Q, int CH, int NBG, int PF, int MINB, int G>
 __global__ void __launch_bounds__(CTA, MINB) k_project(View v, ProjArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_pe;
-    project_item<POL, Q, CH, NBG, PF>(v, a, blockIdx.x, blockIdx.z, blockIdx.y, smem, &s_pe);
+    project_item<POL, Q, CH, NBG, PF, G>(v, a, blockIdx.x, blockIdx.z, blockIdx.y, smem, &s_pe);
 }
 
 // Persistent form over many systems: every CTA takes (system, tile, k*spin) items from a counter until
@@ -396,7 +450,7 @@ __global__ void __launch_bounds__(CTA, MINB) k_project_batch(const View* __restr
         const ProjArgs& a = args[w.x];
         const int nchunks = (a.nbands + BPC * NBG - 1) / (BPC * NBG);
         for (int c = 0; c < nchunks; ++c) {
-            project_item<POL, Q, CH, NBG, PF>(v, a, w.y, w.z, c, smem, &s_pe);
+            project_item<POL, Q, CH, NBG, PF, 0>(v, a, w.y, w.z, c, smem, &s_pe);
             __syncthreads();   // the next chunk or item restages shared memory
         }
     }
@@ -448,25 +502,30 @@ __global__ void k_tile_reduce_batch(const View* __restrict__ views, const ProjAr
     tile_reduce_elem(views[blockIdx.y], args[blockIdx.y].nbands, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-template <int POL, int Q, int CH, int NBG, int PF, int MINB = 2>
+template <int POL, int Q, int CH, int NBG, int PF, int MINB = 2, int G = 0>
 static cudaError_t run_project(const View& v, const ProjArgs& a, cudaStream_t st) {
     static_assert(Q * CH <= TILE_PAD - TILE, "chained loops read up to Q*CH rows past the tile");
-    size_t smem = TILE * sizeof(int) + (size_t)TILE_PAD * v.maxM * (POL == P_F64 ? sizeof(double) : sizeof(float4));
+    size_t smem = TILE * sizeof(int) + (size_t)TILE_PAD * v.maxM * (POL == P_F64 ? sizeof(double) : sizeof(float4)) +
+                  (G ? (size_t)TILE_PAD * 16 : 0);
+    auto fn = k_project<POL, Q, CH, NBG, PF, MINB, G>;
     cudaError_t e = cudaSuccess;
-    if (!smem_configured((const void*)k_project<POL, Q, CH, NBG, PF, MINB>, (int)smem))
-        e = cudaFuncSetAttribute(k_project<POL, Q, CH, NBG, PF, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (!smem_configured((const void*)fn, (int)smem)) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     constexpr int BPC = (CTA / 32) * (32 / Q);
     dim3 grid(v.ntiles, (a.nbands + BPC * NBG - 1) / (BPC * NBG), v.nk * v.ns);
-    k_project<POL, Q, CH, NBG, PF, MINB><<<grid, CTA, smem, st>>>(v, a);
+    fn<<<grid, CTA, smem, st>>>(v, a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_f64_mode mode, int nbands,
-                           int64_t sk, int64_t ss, int64_t sn, int variant, cudaStream_t st) {
+                           int64_t sk, int64_t ss, int64_t sn, int variant, cudaStream_t st, bool gauge) {
     ProjArgs a{psi, sk, ss, sn, nbands};
     cudaError_t e;
-    if (prec == DFTU_C64) {
+    if (gauge) {   // one shape per arithmetic policy with the gauge phases (Sec. V)
+        if (prec == DFTU_C64) e = run_project<P_F32, 8, 16, 4, 0, 2, 1>(v, a, st);
+        else if (mode == DFTU_F64_NATIVE) e = run_project<P_F64, 8, 1, 4, 0, 2, 1>(v, a, st);
+        else e = run_project<P_PAIR, 8, 8, 4, 0, 2, 1>(v, a, st);
+    } else if (prec == DFTU_C64) {
         switch (variant) {   // (lanes per band, points per chain, band groups per CTA)
             case 1: e = run_project<P_F32, 8, 8, 4, 0>(v, a, st); break;
             case 2: e = run_project<P_F32, 16, 8, 4, 0>(v, a, st); break;

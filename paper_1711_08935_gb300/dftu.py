@@ -33,7 +33,8 @@ EXPORTED = ["dftu_create", "dftu_setup_atoms", "dftu_get_sphere", "dftu_coulomb_
             "dftu_set_kernel_variant", "dftu_kernel_variants", "dftu_project_sphere_noalloc",
             "dftu_taylor_step", "dftu_batch_create", "dftu_batch_bind", "dftu_batch_project",
             "dftu_batch_occupations", "dftu_batch_acbn0_uj", "dftu_batch_apply", "dftu_batch_last_error",
-            "dftu_batch_destroy", "dftu_forces", "dftu_radius_cell", "dftu_radius_threshold"]
+            "dftu_batch_destroy", "dftu_forces", "dftu_radius_cell", "dftu_radius_threshold",
+            "dftu_set_vector_potential", "dftu_hubbard_current"]
 
 
 class DftuGrid(C.Structure):
@@ -88,6 +89,8 @@ def load() -> C.CDLL:
         "dftu_batch_last_error": [vp],
         "dftu_batch_destroy": [vp],
         "dftu_forces": [vp, C.POINTER(vp), i32, i32, i64, vp, dp, vp],
+        "dftu_set_vector_potential": [vp, vp, vp],
+        "dftu_hubbard_current": [vp, vp, i32, i32, i64, vp, dp, dp, vp],
         "dftu_radius_cell": [C.POINTER(DftuGrid)],
         "dftu_radius_threshold": [C.POINTER(DftuRadial), d],
         "dftu_get_results": [vp, dp, dp, dp, dp, dp, vp],
@@ -272,6 +275,23 @@ class Handle:
         self._check(self.lib.dftu_forces(self.h, arr, prec, nb, ld, C.c_void_p(f.data_ptr()), _dp(F),
                                          _stream_ptr(stream, self.device)))
         return F
+
+    def set_vector_potential(self, A: Optional[torch.Tensor], stream=None):
+        """Uniform vector potential of the gauge-invariant operator (Sec. V): a float64 CUDA tensor of 3, or None."""
+        if A is not None and (A.dtype != torch.float64 or not A.is_cuda or A.numel() != 3 or not A.is_contiguous()):
+            raise ValueError("A must be a contiguous float64 CUDA tensor of 3 elements")
+        self._A = A   # keep it alive: the phase kernel reads it when it runs
+        ptr = C.c_void_p(A.data_ptr()) if A is not None else None
+        self._check(self.lib.dftu_set_vector_potential(self.h, ptr, _stream_ptr(stream, self.device)))
+
+    def hubbard_current(self, psi: torch.Tensor, f: torch.Tensor, per_atom: bool = False, stream=None):
+        """Hubbard current J [3] (Sec. V, Eq. 17) of the last projected states; with per_atom also [natoms][3]."""
+        prec, nb, ld = self._psi_args(psi)
+        J = np.zeros(3)
+        Jat = np.zeros((self.natoms, 3))
+        self._check(self.lib.dftu_hubbard_current(self.h, C.c_void_p(psi.data_ptr()), prec, nb, ld, C.c_void_p(f.data_ptr()),
+                                                  _dp(J), _dp(Jat), _stream_ptr(stream, self.device)))
+        return (J, Jat) if per_atom else J
 
     def taylor_step(self, psi: torch.Tensor, work: torch.Tensor, f: torch.Tensor, dt: float, order: int = 4, stream=None):
         prec, nb, ld = self._psi_args(psi)

@@ -1,0 +1,156 @@
+"""Parity at the full size of the headline workload (periodic 96^3 oxide supercell, 8 TM d shells + 8 O p
+shells, 256 bands, 8 k-points, 2 spins: 58 GB of complex128 states), in every launch shape the
+benchmark's tuner may pick.
+
+The oracle projects every state (the states are copied to the host in chunks of bands), so the
+projections of all 4096 state rows, the occupation matrices, U, J and E_U are compared in full.  The
+apply is checked on sampled state rows: each apply shape is run in turn on the same states with the
+same projections, so after j applies a sampled row must equal its original plus j times the oracle's
+update of that row.  Tolerances are the ones of the small cases: 1e-12 relative for complex128 states,
+2e-6 for complex64 states, 1e-10 eV for U and J."""
+import dataclasses
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import dftu_oracle as O
+from paper_1711_08935_gb300 import dftu, synth
+from tests._gpu import split_p
+
+pytestmark = pytest.mark.gpu
+EV = O.HARTREE_EV
+NB = 256
+CHUNK = 64
+SAMPLE_ROWS = [(0, 0, 0), (3, 1, 127), (7, 1, 255), (5, 0, 200)]   # (k, spin, band)
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _k_system(s, k):
+    return dataclasses.replace(s, kpts=s.kpts[k:k + 1], wk=s.wk[k:k + 1])
+
+
+def _row_arrays(row_np, spin):
+    """A single state row placed in its spin slot of a [1][2][1][npts] array (zeros in the other slot)."""
+    psi = np.zeros((1, 2, 1, row_np.shape[-1]), dtype=np.complex128)
+    psi[0, spin, 0] = row_np
+    return psi
+
+
+@pytest.fixture(scope="module")
+def workload():
+    dev = torch.device("cuda:0")
+    s = synth.oxide_system()
+    st = O.setup_atoms(s)
+    psi = synth.make_states(s, NB, seed=2, device=dev, spin_bias=synth.afm_spin_bias(s))
+    f_np = synth.step_occupations(s.nk, 2, NB, NB // 2)
+    coul = []
+    for sp in range(len(s.radials)):
+        I = next(i for i, a in enumerate(s.atoms) if a.species == sp)
+        coul.append(O.coulomb_integrals(s.grid, s.atoms[I], st[I]))
+    # oracle projections of every state row, band chunk by band chunk
+    p_ref = [np.zeros((s.nk, 2, NB, 2 * a.l + 1), dtype=np.complex128) for a in s.atoms]
+    for k in range(s.nk):
+        sk = _k_system(s, k)
+        for sp in range(2):
+            for b0 in range(0, NB, CHUNK):
+                chunk = psi[k, sp, b0:b0 + CHUNK].cpu().numpy()
+                pc = O.project(sk, st, chunk[None, None])
+                for I in range(len(s.atoms)):
+                    p_ref[I][k, sp, b0:b0 + CHUNK] = pc[I][0, 0]
+    samples = {r: psi[r].cpu().numpy() for r in SAMPLE_ROWS}
+    yield dict(s=s, st=st, psi=psi, f=f_np, coul=coul, p_ref=p_ref, samples=samples, dev=dev)
+    del psi
+    torch.cuda.empty_cache()
+
+
+def test_full_size_pass_every_shape(workload):
+    w = workload
+    s, st, psi, dev = w["s"], w["st"], w["psi"], w["dev"]
+    fd = torch.from_numpy(w["f"]).to(dev)
+    h = dftu.handle_for_system(s, NB)
+    for sp in range(len(s.radials)):
+        assert rel(h.coulomb_integrals(sp), w["coul"][sp]) < 1e-10
+        h.set_coulomb(sp, w["coul"][sp])
+
+    # ---- projections: every complex128 shape (FP32-pair), the native FP64 path, complex64 states
+    for v in range(h.lib.dftu_kernel_variants(0)):
+        h.set_kernel_variant(0, v)
+        h.project(psi)
+        p = split_p(s, h.projections(NB))
+        for I in range(len(s.atoms)):
+            assert rel(p[I], w["p_ref"][I]) < 1e-12, (v, I)
+    h.set_kernel_variant(0, 0)
+    h.set_f64_mode(dftu.F64_NATIVE)
+    h.project(psi)
+    p = split_p(s, h.projections(NB))
+    assert max(rel(p[I], w["p_ref"][I]) for I in range(len(s.atoms))) < 1e-12
+    h.set_f64_mode(dftu.F64_PAIR)
+    psi32 = psi.to(torch.complex64)
+    for v in range(h.lib.dftu_kernel_variants(1)):
+        h.set_kernel_variant(1, v)
+        h.project(psi32)
+        p = split_p(s, h.projections(NB))
+        assert max(rel(p[I], w["p_ref"][I]) for I in range(len(s.atoms))) < 2e-6, v
+    del psi32
+    torch.cuda.empty_cache()
+
+    # ---- gauge-invariant projections (Sec. V) on the sampled rows, relative to the atom's largest projection
+    A = np.array([0.3, -0.2, 0.25])
+    h.set_vector_potential(torch.tensor(A, dtype=torch.float64, device=dev))
+    h.project(psi)
+    pg = split_p(s, h.projections(NB))
+    for (k, sp, b), row in w["samples"].items():
+        ref = O.project_gauge(_k_system(s, k), st, row[None, None, None], A)
+        for I in range(len(s.atoms)):
+            scale = np.max(np.abs(w["p_ref"][I]))
+            assert np.max(np.abs(pg[I][k, sp, b] - ref[I][0, 0, 0])) < 1e-12 * scale, ((k, sp, b), I)
+    h.set_vector_potential(None)
+
+    # ---- occupations, ACBN0 U and J, E_U from all 4096 rows
+    h.project(psi)
+    h.occupations(fd)
+    h.acbn0_uj()
+    r = h.results()
+    occ = O.occupations(s, w["p_ref"], w["f"])
+    Uref, Jref, Vref, Eref = [], [], [], 0.0
+    for I, at in enumerate(s.atoms):
+        rho, Pb = occ[I]
+        u, j, _ = O.acbn0_uj(rho, Pb, w["coul"][at.species], 2)
+        Uref.append(u); Jref.append(j)
+        Eref += O.hubbard_energy(rho, u - j, 2)
+        Vref.append(np.stack([O.potential(rho[a], u - j) for a in range(2)]))
+        assert np.max(np.abs(r["n"][I] - O.paper_n(rho))) < 1e-12 * max(1.0, np.max(np.abs(rho))), I
+    assert np.max(np.abs(r["U"] - np.array(Uref))) * EV < 1e-10
+    assert np.max(np.abs(r["J"] - np.array(Jref))) * EV < 1e-10
+    assert abs(r["EU"] - Eref) * EV < 1e-10
+    assert h.sync_status() == 0
+
+    # ---- apply: every complex128 shape in turn, sampled rows against orig + j * oracle update
+    deltas = {}
+    for (k, sp, b), row in w["samples"].items():
+        sk = _k_system(s, k)
+        psi_row = _row_arrays(row, sp)
+        p_row = []
+        for I in range(len(s.atoms)):
+            q = np.zeros((1, 2, 1, w["p_ref"][I].shape[-1]), dtype=np.complex128)
+            q[0, sp, 0] = w["p_ref"][I][k, sp, b]
+            p_row.append(q)
+        out = O.apply(sk, st, np.zeros_like(psi_row), p_row, Vref, 1.0)
+        deltas[(k, sp, b)] = out[0, sp, 0]
+    for j, v in enumerate(range(h.lib.dftu_kernel_variants(2)), start=1):
+        h.set_kernel_variant(2, v)
+        h.apply(psi)
+        for key, row in w["samples"].items():
+            got = psi[key].cpu().numpy()
+            # the update itself: the pair sum of phi_m c_m errs by ~2^-44 of max|phi| max|c|, which can exceed
+            # the update's own size (cancellation over m) by a few times, and each FP64 addition into psi
+            # rounds at 1e-16 of |psi|; 1e-10 of the update still fails on any wrong term, sign or phase
+            upd_scale = max(np.max(np.abs(j * deltas[key])), 1e-5 * np.max(np.abs(row)))
+            assert np.max(np.abs((got - row) - j * deltas[key])) < 1e-10 * upd_scale, (v, key)
+            assert rel(got, row + j * deltas[key]) < 1e-12, (v, key)
+    h.close()

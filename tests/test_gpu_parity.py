@@ -241,10 +241,15 @@ def test_argument_and_order_errors():
     assert e.value.status == dftu.DFTU_ERR_INVALID_ARG
 
 
+NBV = 150
+
+
 @pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
 def test_every_kernel_variant_matches_oracle(dtype):
-    """The autotuner may pick any shape variant: each must give the oracle's projections and applied states."""
-    s, psi, f = _collinear_case("small_oxide", nb=37, seed=13)
+    """The autotuner may pick any shape variant: each must give the oracle's projections and applied states.
+    150 bands fill more than two band groups of every shape (64 bands per group at 4 lanes per band)
+    and leave a ragged last group."""
+    s, psi, f = _collinear_case("small_oxide", nb=NBV, seed=13)
     st = O.setup_atoms(s)
     fixed = [(0.3, 0.02), (0.25, 0.01), (0.4, 0.05), (0.2, 0.0)]
     ref = O.hubbard_pass(s, st, psi, f, fixed_u=fixed)
@@ -252,14 +257,14 @@ def test_every_kernel_variant_matches_oracle(dtype):
     lib = dftu.load()
     nvar = lib.dftu_kernel_variants(0)
     for var in range(nvar):
-        h = dftu.handle_for_system(s, 37)
+        h = dftu.handle_for_system(s, NBV)
         for I, (u, j) in enumerate(fixed):
             h.set_u(I, u, j)
         h.set_kernel_variant(0 if fp64 else 1, var)
         h.set_kernel_variant(2 if fp64 else 3, var)
         t = torch.from_numpy(psi).cuda().to(dtype)
         h.project(t)
-        p = split_p(s, h.projections(37))
+        p = split_p(s, h.projections(NBV))
         for I in range(len(s.atoms)):
             assert rel(p[I], ref["p"][I]) < (1e-12 if fp64 else 2e-6), (var, I)
         h.occupations(torch.from_numpy(f).cuda())
