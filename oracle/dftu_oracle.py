@@ -13,6 +13,7 @@ equation.  Equation numbers below are those printed in the paper:
   Eq. (8)  renormalised density matrix  Pbar                   (Sec. III)
   Eq. (9)  renormalised occupation      Nbar                   (Sec. III)
   Eq. (10) ACBN0 Ubar,  Eq. (11) ACBN0 Jbar                    (Sec. III)
+  Eq. (A1) Hartree-Fock energy of the shell, Eq. (A3) FLL double counting with the m.m term
   Eq. (A2) non-collinear occupations, Eq. (A5) non-collinear E_U        (App. A)
   Eq. (B2) Coulomb integrals, Eqs. (B3)-(B6) non-collinear ACBN0        (App. B)
 
@@ -35,6 +36,10 @@ Readings of points the paper leaves open (each is also recorded in the design no
     counts that channel twice.
   * A denominator below 1e-14 gives U = J = 0 for that atom and raises the zero-denominator flag.
   * Non-collinear orbitals are spin independent; Nbar sums |p|^2 over both spinor components.
+  * Eq. (A1) is printed for occupation matrices diagonal in the orbital index; it is evaluated on
+    the orbital-diagonal entries n^{ss'}_{mm} as printed, whatever the off-diagonal ones are.
+    Eq. (A3) uses N = Tr n and the moment m_i = Tr_s(sigma_i rho_s), rho_s = Tr_l n.  Collinear
+    channels are spin-diagonal blocks (an unpolarised channel stands for both spins).
 """
 from __future__ import annotations
 
@@ -391,6 +396,47 @@ def hubbard_energy_nc(rho: np.ndarray, Ueff: float) -> float:
     """Eq. (A5): (U-J)/2 [sum_{s,m} n^{ss}_mm - sum n^{ss'}_{mm'} n^{s's}_{m'm}], 2M x 2M matrix."""
     n = paper_n(rho)
     return 0.5 * Ueff * float(np.real(np.trace(n) - np.einsum("ab,ba->", n, n)))
+
+
+# ------------------------------------------------------------------------------------------------
+# Fully-localised-limit decomposition (App. A): E_ee of Eq. (A1) and E_DC of Eq. (A3)
+# ------------------------------------------------------------------------------------------------
+
+def spin_blocks(rho: np.ndarray, noncollinear: bool, nspin: int) -> np.ndarray:
+    """The paper's n as a [2][2][M][M] array n[s][s'][m][m'] = n^{ss'}_{mm'} from the stored rho
+    (n^T): non-collinear 2M x 2M in the combined index s*M + m, collinear [ns][M][M]."""
+    n = paper_n(rho)
+    if noncollinear:
+        M = n.shape[-1] // 2
+        return n.reshape(2, M, 2, M).transpose(0, 2, 1, 3)
+    M = n.shape[-1]
+    out = np.zeros((2, 2, M, M), dtype=np.complex128)
+    out[0, 0] = n[0]
+    out[1, 1] = n[1] if nspin == 2 else n[0]
+    return out
+
+
+def fll_energy(rho: np.ndarray, U: float, J: float, noncollinear: bool, nspin: int = 2):
+    """Eq. (A1) and Eq. (A3) for one shell.  Returns (E_ee, E_DC); E_ee - E_DC is the FLL energy.
+
+    E_ee = U/2 sum_s sum_{m,m'} n^{ss}_mm n^{-s-s}_m'm' - U/2 sum_s sum_m n^{s-s}_mm n^{-ss}_mm
+           - J/2 sum_s sum_{m != m'} n^{s-s}_mm n^{-ss}_m'm' + (U-J)/2 sum_s sum_{m != m'} n^{ss}_mm n^{ss}_m'm'
+    E_DC = U/2 N (N - 1) - J/2 N (N/2 - 1) - J/4 m.m"""
+    nb = spin_blocks(rho, noncollinear, nspin)
+    d = np.array([[np.diagonal(nb[s, t]) for t in range(2)] for s in range(2)])   # d[s][t][m] = n^{st}_mm
+    e_ee = 0.0 + 0.0j
+    for s in range(2):
+        o = 1 - s
+        e_ee += 0.5 * U * np.sum(d[s, s]) * np.sum(d[o, o])
+        e_ee -= 0.5 * U * np.sum(d[s, o] * d[o, s])
+        e_ee -= 0.5 * J * (np.sum(d[s, o]) * np.sum(d[o, s]) - np.sum(d[s, o] * d[o, s]))
+        e_ee += 0.5 * (U - J) * (np.sum(d[s, s]) ** 2 - np.sum(d[s, s] * d[s, s]))
+    rho_s = np.array([[np.sum(d[s, t]) for t in range(2)] for s in range(2)])     # Tr_l n, [s][s']
+    pauli = [np.array([[0, 1], [1, 0]]), np.array([[0, -1j], [1j, 0]]), np.array([[1, 0], [0, -1]])]
+    mvec = np.array([np.trace(P @ rho_s) for P in pauli])
+    N = np.trace(rho_s)
+    e_dc = 0.5 * U * N * (N - 1) - 0.5 * J * N * (0.5 * N - 1) - 0.25 * J * np.sum(mvec * mvec)
+    return float(np.real(e_ee)), float(np.real(e_dc))
 
 
 def potential(rho: np.ndarray, Ueff: float) -> np.ndarray:

@@ -492,3 +492,82 @@ def test_hubbard_current_is_energy_derivative_in_A():
         dE = (E(A0 + e) - E(A0 - e)) / (2 * eps)
         assert abs(J[a] - dE) < 1e-8 * max(1.0, abs(dE)), (a, J[a], dE)
     assert np.max(np.abs(J)) > 1e-6
+
+
+# ---- App. A: fully-localised-limit decomposition, Eq. (A1) minus Eq. (A3)
+
+def _nc_rho_from_paper_n(n4):
+    """Stored rho (n^T, combined index s*M + m) from the paper's n[s][s'][m][m']."""
+    M = n4.shape[-1]
+    n = n4.transpose(0, 2, 1, 3).reshape(2 * M, 2 * M)
+    return n.T.copy()
+
+
+def _spinor(theta, phi):
+    return np.array([math.cos(theta / 2), np.exp(1j * phi) * math.sin(theta / 2)])
+
+
+def test_fll_energy_vanishes_for_integer_occupations():
+    """The FLL energy E_ee - E_DC is zero whenever every orbital is either empty or filled with one
+    electron of a definite spin (Sec. III / App. A: the functional corrects only fractional occupations):
+    collinear subsets, a full shell, and one or two electrons with a spinor of any direction."""
+    U, J = 0.31, 0.07
+    rng = np.random.default_rng(3)
+    M = 5
+    for _ in range(6):
+        occ = rng.integers(0, 2, size=(2, M)).astype(float)
+        rho = np.stack([np.diag(occ[0]), np.diag(occ[1])]).astype(np.complex128)
+        e_ee, e_dc = O.fll_energy(rho, U, J, noncollinear=False, nspin=2)
+        assert abs(e_ee - e_dc) < 1e-13
+    full = np.stack([np.eye(M), np.eye(M)]).astype(np.complex128)
+    e_ee, e_dc = O.fll_energy(full, U, J, noncollinear=False, nspin=2)
+    assert abs(e_ee - e_dc) < 1e-13 and abs(e_dc) > 1.0
+    for theta, phi in [(0.3, 1.1), (1.9, -2.4), (math.pi / 2, 0.0)]:
+        chi = _spinor(theta, phi)
+        for orbitals in ([2], [0, 3]):                          # one electron; two with the same spinor
+            n4 = np.zeros((2, 2, M, M), dtype=np.complex128)
+            for m in orbitals:
+                n4[:, :, m, m] = np.outer(chi, np.conj(chi))    # n^{ss'}_mm = chi_s conj(chi_s')
+            e_ee, e_dc = O.fll_energy(_nc_rho_from_paper_n(n4), U, J, noncollinear=True)
+            assert abs(e_ee - e_dc) < 1e-13, (theta, phi, orbitals)
+            assert abs(e_ee) > 1e-3 or len(orbitals) == 1
+
+
+def test_fll_energy_equals_dudarev_for_diagonal_collinear_occupations():
+    """For orbital-diagonal collinear n, Eq. (A1) minus Eq. (A3) reduces to the Dudarev energy Eq. (3)
+    with U_eff = U - J, for spin-polarised and unpolarised channels."""
+    U, J = 0.42, 0.09
+    rng = np.random.default_rng(8)
+    for nspin in (2, 1):
+        for M in (3, 5, 7):
+            occ = rng.uniform(0, 1, size=(nspin, M))
+            rho = np.stack([np.diag(o) for o in occ]).astype(np.complex128)
+            e_ee, e_dc = O.fll_energy(rho, U, J, noncollinear=False, nspin=nspin)
+            ref = O.hubbard_energy(rho, U - J, nspin)
+            assert abs((e_ee - e_dc) - ref) < 1e-13 * max(1.0, abs(ref)), (nspin, M)
+            assert abs(ref) > 1e-3
+
+
+def test_fll_double_counting_moment_term():
+    """E_DC of Eq. (A3) for one orbital with spin density matrix [[a, c], [conj c, b]]: N = a + b and
+    m.m = (a - b)^2 + 4|c|^2 (Pauli matrices), and E_DC is unchanged by a global spin rotation."""
+    U, J = 0.5, 0.12
+    a, b, c = 0.7, 0.2, 0.25 - 0.1j
+    M = 3
+    n4 = np.zeros((2, 2, M, M), dtype=np.complex128)
+    n4[0, 0, 1, 1], n4[1, 1, 1, 1], n4[0, 1, 1, 1], n4[1, 0, 1, 1] = a, b, c, np.conj(c)
+    _, e_dc = O.fll_energy(_nc_rho_from_paper_n(n4), U, J, noncollinear=True)
+    N, mm = a + b, (a - b) ** 2 + 4 * abs(c) ** 2
+    assert abs(e_dc - (0.5 * U * N * (N - 1) - 0.5 * J * N * (0.5 * N - 1) - 0.25 * J * mm)) < 1e-15
+    # a general Hermitian n rotated in spin space: E_DC is invariant, E_ee in general is not
+    rng = np.random.default_rng(4)
+    X = rng.normal(size=(2 * M, 2 * M)) + 1j * rng.normal(size=(2 * M, 2 * M))
+    n = 0.1 * (X @ X.conj().T)
+    th, ph = 0.8, -1.3
+    R2 = np.array([[math.cos(th / 2), -np.exp(-1j * ph) * math.sin(th / 2)],
+                   [np.exp(1j * ph) * math.sin(th / 2), math.cos(th / 2)]])
+    R = np.kron(R2, np.eye(M))
+    n_rot = R @ n @ R.conj().T
+    _, d0 = O.fll_energy(n.T.copy(), U, J, noncollinear=True)
+    _, d1 = O.fll_energy(n_rot.T.copy(), U, J, noncollinear=True)
+    assert abs(d0 - d1) < 1e-12 * abs(d0)
