@@ -199,6 +199,18 @@ dftu_status dftu_set_vector_potential(dftu_handle h, const double* A, dftu_strea
 dftu_status dftu_hubbard_current(dftu_handle h, const void* psi, dftu_prec prec, int nbands, int64_t ld_band,
                                  const double* f, double* J_out, double* J_atom_out, dftu_stream stream);
 
+/* Fully-localised-limit decomposition of the shell energy (App. A) for every atom, with the U and J of
+ * the last dftu_acbn0_uj (ACBN0, or the values fixed by dftu_set_u):
+ *   E_ee = U/2 sum_s sum_{mm'} n^{ss}_mm n^{-s-s}_m'm' - U/2 sum_s sum_m n^{s-s}_mm n^{-ss}_mm
+ *          - J/2 sum_s sum_{m!=m'} n^{s-s}_mm n^{-ss}_m'm' + (U-J)/2 sum_s sum_{m!=m'} n^{ss}_mm n^{ss}_m'm'   (Eq. A1)
+ *   E_DC = U/2 N(N-1) - J/2 N(N/2-1) - J/4 m.m,  N = Tr n,  m_i = Tr_s(sigma_i Tr_l n)                (Eq. A3)
+ * E_ee is evaluated on the orbital-diagonal entries n^{ss'}_mm, the form the paper prints (it assumes
+ * diagonal occupation matrices); E_ee - E_DC equals the Dudarev E_U of Eq. (3) / (A5) when n is
+ * orbital-diagonal and collinear.  Collinear handles use the spin-diagonal blocks (an unpolarised
+ * channel stands for both spins).  Eee_out, Edc_out: host [natoms] in Hartree, either may be NULL
+ * (not both).  Blocking on stream.  The reported E_U and the potential are not changed by this call. */
+dftu_status dftu_fll_energy(dftu_handle h, double* Eee_out, double* Edc_out, dftu_stream stream);
+
 /* Hubbard forces (Sec. IV) on every atom, in the form that differentiates the states: with
  * g_a = <phi_a|d_i psi> and p_a = <phi_a|psi>,
  *   F_{I,i} = -sum_{spin blocks} sum_{ab} V_ab sum_{k,n} w_k f [conj(g_a) p_b + conj(p_a) g_b]

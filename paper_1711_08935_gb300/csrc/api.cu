@@ -405,6 +405,7 @@ dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, 
     if (e == cudaSuccess) e = dalloc(c, &v.pgrad, (size_t)3 * rowsP * c->max_bands * MT);
     if (e == cudaSuccess) e = dalloc(c, &c->d_forces, (size_t)3 * natoms);
     if (e == cudaSuccess) e = dalloc(c, &c->d_current, (size_t)3 * natoms);
+    if (e == cudaSuccess) e = dalloc(c, &c->d_fll, (size_t)2 * natoms);
     if (e == cudaSuccess) e = dalloc(c, &v.gauge_d, (size_t)c->S);
     if (e == cudaSuccess) e = dalloc(c, &v.gauge_f, (size_t)c->S);
     if (e == cudaSuccess) e = dalloc(c, &v.phid64, (size_t)3 * phi_off);
@@ -742,6 +743,27 @@ dftu_status dftu_hubbard_current(dftu_handle h, const void* psi, dftu_prec prec,
         J_out[0] = J_out[1] = J_out[2] = 0.0;
         for (int a = 0; a < na; ++a)
             for (int d = 0; d < 3; ++d) J_out[d] += Jat[3 * a + d];
+    }
+    c->last_stream = st;
+    return DFTU_OK;
+}
+
+dftu_status dftu_fll_energy(dftu_handle h, double* Eee_out, double* Edc_out, dftu_stream stream) {
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c) return DFTU_ERR_INVALID_ARG;
+    if (!c->pot_ready) return fail(c, DFTU_ERR_NOT_READY, "fll_energy: call dftu_occupations and dftu_acbn0_uj first");
+    if (!Eee_out && !Edc_out) return fail(c, DFTU_ERR_INVALID_ARG, "fll_energy: both outputs are NULL");
+    Guard g(c->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int na = (int)c->atoms.size();
+    std::vector<double> out(2 * (size_t)na);
+    cudaError_t e = launch_fll(c->v, c->d_fll, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out.data(), c->d_fll, out.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "fll_energy");
+    for (int a = 0; a < na; ++a) {
+        if (Eee_out) Eee_out[a] = out[2 * a];
+        if (Edc_out) Edc_out[a] = out[2 * a + 1];
     }
     c->last_stream = st;
     return DFTU_OK;

@@ -128,6 +128,7 @@ struct Ctx {
     double* d_taylor = nullptr;      // [MAX_TAYLOR] complex Taylor coefficients -i dt / j
     double* d_forces = nullptr;      // [natoms][3]
     double* d_current = nullptr;     // [natoms][3] per-atom Hubbard current
+    double* d_fll = nullptr;         // [natoms][2] E_ee, E_DC of App. A
     std::vector<int> h_coul_set;     // host copies, so hot-path calls never read the device
     std::vector<double> h_fixU;
 };
@@ -181,6 +182,7 @@ cudaError_t launch_displaced_orbitals(const View& v, int64_t phi_total, cudaStre
 cudaError_t launch_current(const View& v, const double* f, int nbands, double* Jat, cudaStream_t st);
 cudaError_t launch_taylor_coefs(double dt, int order, double* coefs, cudaStream_t st);
 cudaError_t launch_forces(const View& v, const double* f, int nbands, double* F, cudaStream_t st);
+cudaError_t launch_fll(const View& v, double* out, cudaStream_t st);
 cudaError_t launch_project_batch(const BatchLaunch& b, dftu_prec prec, dftu_f64_mode mode, int variant, cudaStream_t st);
 cudaError_t launch_occupations_batch(const BatchLaunch& b, cudaStream_t st);
 cudaError_t launch_acbn0_batch(const BatchLaunch& b, cudaStream_t st);

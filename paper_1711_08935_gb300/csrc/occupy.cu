@@ -302,6 +302,60 @@ cudaError_t launch_forces(const View& v, const double* f, int nbands, double* F,
     return cudaGetLastError();
 }
 
+// Fully-localised-limit decomposition of App. A for each atom: E_ee of Eq. (A1), evaluated on the
+// orbital-diagonal entries n^{st}_mm (the form the paper prints), and the double counting E_DC of
+// Eq. (A3) with N = Tr n and the moment m_i = Tr_s(sigma_i Tr_l n).  One thread per atom, FP64.
+// out[atom] = (E_ee, E_DC).
+__global__ void k_fll(View v, double2* __restrict__ out) {
+    const int a = blockIdx.x;
+    if (threadIdx.x != 0) return;
+    const int M = v.atom_M[a];
+    const double2* r = v.rho + v.atom_mat_off[a];
+    const double2 zero = make_double2(0.0, 0.0);
+    double2 d[2][2][MAXM];
+    for (int s = 0; s < 2; ++s)
+        for (int t = 0; t < 2; ++t)
+            for (int m = 0; m < M; ++m) {
+                if (v.noncollinear) d[s][t][m] = r[(t * M + m) * (2 * M) + s * M + m];   // rho = n^T
+                else d[s][t][m] = (s == t) ? r[(v.ns == 2 ? s : 0) * M * M + m * M + m] : zero;
+            }
+    double2 tr[2][2];
+    for (int s = 0; s < 2; ++s)
+        for (int t = 0; t < 2; ++t) {
+            double2 x = zero;
+            for (int m = 0; m < M; ++m) { x.x += d[s][t][m].x; x.y += d[s][t][m].y; }
+            tr[s][t] = x;
+        }
+    auto re_mul = [](double2 x, double2 y) { return x.x * y.x - x.y * y.y; };
+    const double U = v.U[a], J = v.J[a];
+    double ee = 0.0;
+    for (int s = 0; s < 2; ++s) {
+        const int o = 1 - s;
+        double flip = 0.0, same = 0.0;
+        for (int m = 0; m < M; ++m) {
+            flip += re_mul(d[s][o][m], d[o][s][m]);
+            same += re_mul(d[s][s][m], d[s][s][m]);
+        }
+        ee += 0.5 * U * re_mul(tr[s][s], tr[o][o]);
+        ee -= 0.5 * U * flip;
+        ee -= 0.5 * J * (re_mul(tr[s][o], tr[o][s]) - flip);
+        ee += 0.5 * (U - J) * (re_mul(tr[s][s], tr[s][s]) - same);
+    }
+    // m_x = rho_10 + rho_01, m_y = i (rho_01 - rho_10), m_z = rho_00 - rho_11 (rho = Tr_l n, [s][s'])
+    const double2 mx = make_double2(tr[1][0].x + tr[0][1].x, tr[1][0].y + tr[0][1].y);
+    const double2 my = make_double2(-(tr[0][1].y - tr[1][0].y), tr[0][1].x - tr[1][0].x);
+    const double2 mz = make_double2(tr[0][0].x - tr[1][1].x, tr[0][0].y - tr[1][1].y);
+    const double mm = re_mul(mx, mx) + re_mul(my, my) + re_mul(mz, mz);
+    const double N = tr[0][0].x + tr[1][1].x;
+    const double dc = 0.5 * U * N * (N - 1.0) - 0.5 * J * N * (0.5 * N - 1.0) - 0.25 * J * mm;
+    out[a] = make_double2(ee, dc);
+}
+
+cudaError_t launch_fll(const View& v, double* out, cudaStream_t st) {
+    k_fll<<<v.natoms, 32, 0, st>>>(v, reinterpret_cast<double2*>(out));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_nbar(const View& v, int nbands, cudaStream_t st) {
     int rows = v.noncollinear ? v.nk : v.nk * v.ns;
     int64_t n = (int64_t)rows * nbands;

@@ -34,7 +34,7 @@ EXPORTED = ["dftu_create", "dftu_setup_atoms", "dftu_get_sphere", "dftu_coulomb_
             "dftu_taylor_step", "dftu_batch_create", "dftu_batch_bind", "dftu_batch_project",
             "dftu_batch_occupations", "dftu_batch_acbn0_uj", "dftu_batch_apply", "dftu_batch_last_error",
             "dftu_batch_destroy", "dftu_forces", "dftu_radius_cell", "dftu_radius_threshold",
-            "dftu_set_vector_potential", "dftu_hubbard_current"]
+            "dftu_set_vector_potential", "dftu_hubbard_current", "dftu_fll_energy"]
 
 
 class DftuGrid(C.Structure):
@@ -91,6 +91,7 @@ def load() -> C.CDLL:
         "dftu_forces": [vp, C.POINTER(vp), i32, i32, i64, vp, dp, vp],
         "dftu_set_vector_potential": [vp, vp, vp],
         "dftu_hubbard_current": [vp, vp, i32, i32, i64, vp, dp, dp, vp],
+        "dftu_fll_energy": [vp, dp, dp, vp],
         "dftu_radius_cell": [C.POINTER(DftuGrid)],
         "dftu_radius_threshold": [C.POINTER(DftuRadial), d],
         "dftu_get_results": [vp, dp, dp, dp, dp, dp, vp],
@@ -292,6 +293,12 @@ class Handle:
         self._check(self.lib.dftu_hubbard_current(self.h, C.c_void_p(psi.data_ptr()), prec, nb, ld, C.c_void_p(f.data_ptr()),
                                                   _dp(J), _dp(Jat), _stream_ptr(stream, self.device)))
         return (J, Jat) if per_atom else J
+
+    def fll_energy(self, stream=None):
+        """(E_ee, E_DC) per atom (Hartree), App. A Eqs. (A1) and (A3), with the current U and J."""
+        ee, dc = np.zeros(self.natoms), np.zeros(self.natoms)
+        self._check(self.lib.dftu_fll_energy(self.h, _dp(ee), _dp(dc), _stream_ptr(stream, self.device)))
+        return ee, dc
 
     def taylor_step(self, psi: torch.Tensor, work: torch.Tensor, f: torch.Tensor, dt: float, order: int = 4, stream=None):
         prec, nb, ld = self._psi_args(psi)
