@@ -18,6 +18,12 @@
  *     DFTU_C128, complex64 for DFTU_C64).  Layout, with ld_band >= npts elements between bands:
  *       collinear / unpolarised: psi[k][spin][band][ld_band]  (spin extent 2 or 1)
  *       non-collinear:           psi[k][band][component][ld_band] (component extent 2)
+ *   - State arrays (psi, work, gradients) may live in this GPU's memory, in managed memory, or in
+ *     page-locked host memory (cudaHostAlloc / cudaHostRegister, mapped at the same address), or in
+ *     any host memory when the GPU reads pageable memory.  Host-resident states are read and
+ *     written by the kernels directly over the host link: only the sphere points move.  Other
+ *     pointers are refused with DFTU_ERR_INVALID_ARG; the check is skipped while the stream is
+ *     capturing a graph.
  *   - psi is the full Bloch function on the cell.  A sphere point at unfolded position r_u folds
  *     to r_w = r_u - T; the gather multiplies psi(r_w) by exp(+i k.T), the scatter by exp(-i k.T).
  *   - Occupation matrices are reported as the paper's n_{mm'} = sum w f <psi|phi_m><phi_m'|psi>.
@@ -137,7 +143,7 @@ dftu_status dftu_set_kernel_variant(dftu_handle h, int which, int variant);
 int dftu_kernel_variants(int which);
 
 /* Projections p^{k,s}_{I,m,n} = dV sum_j phi_{I,m}(j) exp(+i k.T_j) psi_{k,s,n}(idx_j) of the first
- * nbands bands (nbands <= max_bands) of psi (device, layout above) onto every atom's orbitals.
+ * nbands bands (nbands <= max_bands) of psi (layout and memory above) onto every atom's orbitals.
  * DFTU_C64 states are multiplied by FP32 orbitals with an FP32 low-part correction, summed in FP32
  * within a point tile and in FP64 across tiles; DFTU_C128 follows dftu_set_f64_mode.
  * The result stays on the device for the calls below. */

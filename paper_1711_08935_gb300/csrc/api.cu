@@ -55,6 +55,30 @@ bool valid_stride_args(Ctx* c, int nbands, int64_t ld) {
     return nbands >= 1 && nbands <= c->max_bands && ld >= (int64_t)c->grid.n[0] * c->grid.n[1] * c->grid.n[2];
 }
 
+}  // namespace
+
+bool dftu::gpu_addressable(int device, const void* p, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return true;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    if (a.type == cudaMemoryTypeDevice) return a.device == device;
+    if (a.type == cudaMemoryTypeHost) return a.devicePointer == p;
+    int pageable = 0;
+    cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, device);
+    return pageable != 0;
+}
+
+namespace {
+
 void strides(const Ctx* c, int nbands, int64_t ld, int64_t& sk, int64_t& ss, int64_t& sn) {
     if (c->spin == DFTU_NONCOLLINEAR) {
         ss = ld;
@@ -562,6 +586,7 @@ dftu_status dftu_project(dftu_handle h, const void* psi, dftu_prec prec, int nba
     int64_t sk, ss, sn;
     strides(c, nbands, ld_band, sk, ss, sn);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!gpu_addressable(c->device, psi, st)) return fail(c, DFTU_ERR_INVALID_ARG, "project: the states are not addressable by this GPU (device memory of another GPU, or pageable host memory on a device without pageable access)");
     cudaError_t e = launch_project(c->v, psi, prec, c->f64_mode, nbands, sk, ss, sn, c->variant[prec == DFTU_C64 ? 1 : 0], st,
                                    c->gauge_on);
     if (e != cudaSuccess) return cuda_fail(c, e, "project");
@@ -615,6 +640,7 @@ dftu_status dftu_apply(dftu_handle h, void* psi_out, dftu_prec prec, int nbands,
     int64_t sk, ss, sn;
     strides(c, nbands, ld_band, sk, ss, sn);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!gpu_addressable(c->device, psi_out, st)) return fail(c, DFTU_ERR_INVALID_ARG, "apply: the states are not addressable by this GPU (device memory of another GPU, or pageable host memory on a device without pageable access)");
     cudaError_t e = launch_apply(c->v, psi_out, prec, c->f64_mode, nbands, sk, ss, sn, coef ? coef : c->d_coef_one,
                                  c->d_color_order, c->color_beg, c->variant[prec == DFTU_C64 ? 3 : 2], accumulate ? 1 : 0, st,
                                  c->gauge_on);
@@ -638,6 +664,7 @@ dftu_status dftu_taylor_step(dftu_handle h, void* psi, void* work, dftu_prec pre
     int64_t sk, ss, sn;
     strides(c, nbands, ld_band, sk, ss, sn);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!gpu_addressable(c->device, psi, st) || !gpu_addressable(c->device, work, st)) return fail(c, DFTU_ERR_INVALID_ARG, "taylor_step: the states are not addressable by this GPU (device memory of another GPU, or pageable host memory on a device without pageable access)");
     const int vp = c->variant[prec == DFTU_C64 ? 1 : 0], va = c->variant[prec == DFTU_C64 ? 3 : 2];
     const bool G = c->gauge_on;
     cudaError_t e = launch_project(c->v, psi, prec, c->f64_mode, nbands, sk, ss, sn, vp, st, G);
@@ -673,6 +700,8 @@ dftu_status dftu_forces(dftu_handle h, const void* const* dpsi, dftu_prec prec, 
     int64_t sk, ss, sn;
     strides(c, nbands, ld_band, sk, ss, sn);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    for (int i = 0; i < 3; ++i)
+        if (!gpu_addressable(c->device, dpsi[i], st)) return fail(c, DFTU_ERR_INVALID_ARG, "forces: the states are not addressable by this GPU (device memory of another GPU, or pageable host memory on a device without pageable access)");
     const int64_t gstride = (int64_t)c->nk * c->ns * c->max_bands * c->MT;
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
@@ -722,6 +751,7 @@ dftu_status dftu_hubbard_current(dftu_handle h, const void* psi, dftu_prec prec,
     int64_t sk, ss, sn;
     strides(c, nbands, ld_band, sk, ss, sn);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!gpu_addressable(c->device, psi, st)) return fail(c, DFTU_ERR_INVALID_ARG, "hubbard_current: the states are not addressable by this GPU (device memory of another GPU, or pageable host memory on a device without pageable access)");
     const int64_t gstride = (int64_t)c->nk * c->ns * c->max_bands * c->MT;
     cudaError_t e = cudaSuccess;
     for (int a = 0; a < 3 && e == cudaSuccess; ++a) {

@@ -183,6 +183,11 @@ cudaError_t launch_current(const View& v, const double* f, int nbands, double* J
 cudaError_t launch_taylor_coefs(double dt, int order, double* coefs, cudaStream_t st);
 cudaError_t launch_forces(const View& v, const double* f, int nbands, double* F, cudaStream_t st);
 cudaError_t launch_fll(const View& v, double* out, cudaStream_t st);
+// True when GPU `device` can address p: its own or managed memory, page-locked host memory mapped at
+// the same address (cudaHostAlloc / cudaHostRegister), or any host memory when the device reads
+// pageable memory (address translation over the host link).  While `st` is capturing a graph the
+// check is skipped (pointers are checked when the work is set up eagerly).
+bool gpu_addressable(int device, const void* p, cudaStream_t st);
 cudaError_t launch_project_batch(const BatchLaunch& b, dftu_prec prec, dftu_f64_mode mode, int variant, cudaStream_t st);
 cudaError_t launch_occupations_batch(const BatchLaunch& b, cudaStream_t st);
 cudaError_t launch_acbn0_batch(const BatchLaunch& b, cudaStream_t st);

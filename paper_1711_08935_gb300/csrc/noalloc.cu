@@ -109,6 +109,7 @@ extern "C" dftu_status dftu_project_sphere_noalloc(const void* psi, dftu_prec pr
     double2* part = scratch_for_current_device(dev);
     if (!part) return DFTU_ERR_CUDA;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!dftu::gpu_addressable(dev, psi, st)) return DFTU_ERR_INVALID_ARG;
     if (prec == DFTU_C128)
         k_na_tiles<double2><<<ntiles, NA_CTA, 0, st>>>(static_cast<const double2*>(psi), nbands, ld_band, idx,
                                                         reinterpret_cast<const double2*>(phase), phi, npts, M, dV, part);

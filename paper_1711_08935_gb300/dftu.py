@@ -229,8 +229,8 @@ class Handle:
             prec = C64
         else:
             raise TypeError("psi must be complex128 or complex64")
-        if not psi.is_cuda or not psi.is_contiguous():
-            raise ValueError("psi must be a contiguous CUDA tensor")
+        if not psi.is_contiguous() or not (psi.is_cuda or psi.is_pinned()):
+            raise ValueError("psi must be a contiguous CUDA tensor or a contiguous pinned host tensor")
         if self.spin == NONCOLLINEAR:
             if psi.dim() != 4 or psi.shape[0] != self.nk or psi.shape[2] != 2:
                 raise ValueError("non-collinear psi must be [nk][nbands][2][npts]")
