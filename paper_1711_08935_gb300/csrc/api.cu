@@ -438,6 +438,9 @@ dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, 
     if (e == cudaSuccess) e = dalloc(c, &v.nbar, (size_t)rowsN * c->max_bands * nspecies);
     if (e == cudaSuccess) e = dalloc(c, &v.rho, (size_t)mat);
     if (e == cudaSuccess) e = dalloc(c, &v.pbar, (size_t)mat);
+    if (e == cudaSuccess) e = dalloc(c, &v.occ_part, (size_t)natoms * 2 * OCC_SPLIT * 2 * OCC_MAXP);
+    if (e == cudaSuccess) e = dalloc(c, &v.occ_count, (size_t)natoms * 2);
+    if (e == cudaSuccess) e = cudaMemset(v.occ_count, 0, (size_t)natoms * 2 * sizeof(int));
     if (e == cudaSuccess) e = dalloc(c, &v.V, (size_t)mat);
     if (e == cudaSuccess) e = dalloc(c, &v.U, (size_t)natoms);
     if (e == cudaSuccess) e = dalloc(c, &v.J, (size_t)natoms);

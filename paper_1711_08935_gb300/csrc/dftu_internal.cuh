@@ -17,6 +17,8 @@ constexpr int IMG_RANGE = 2;   // lattice images |T| <= 2 cells per axis
 constexpr int NIMG = 125;      // (2*IMG_RANGE+1)^3 image ids
 constexpr int CTA = 256;       // threads per CTA of the streaming kernels
 constexpr int MAX_TAYLOR = 8;  // highest Taylor order of dftu_taylor_step
+constexpr int OCC_SPLIT = 8;   // CTAs sharing the (k, band) sum of one occupation matrix
+constexpr int OCC_MAXP = (2 * MAXM) * (2 * MAXM);   // largest matrix (non-collinear f shell), elements
 
 enum StatusBits : int { ST_NONFINITE = 1, ST_ZERO_DENOM = 2, ST_TIMEOUT = 4 };
 
@@ -82,6 +84,8 @@ struct View {
     double* nbar;          // collinear [nk*ns][max_bands][nspecies]; non-collinear [nk][max_bands][nspecies]
     double2* rho;          // per atom: collinear [ns][M][M]; non-collinear [2M][2M]   (rho = n^T)
     double2* pbar;         // same layout, renormalised (Eq. 8), transposed like rho
+    double2* occ_part;     // [natoms][2][OCC_SPLIT][2][OCC_MAXP] partial rho / Pbar sums of the split CTAs
+    int* occ_count;        // [natoms][2] CTAs done per matrix; zero between launches
     double2* V;            // same layout, U_eff (1/2 - rho)
     const double* coul;
     const int* coul_set;   // [nspecies] 1 if set

@@ -37,9 +37,13 @@ __global__ void k_nbar_batch(const View* __restrict__ views, const ProjArgs* __r
     nbar_elem(views[blockIdx.y], args[blockIdx.y].nbands, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-// Eqs. (4), (8), (A2), (B3): one CTA per (atom, spin channel) [collinear] or per atom [non-collinear].
-// Thread (pair, slice): pair = matrix element (a,b); slices split the (k, band) sum, reduced in order.
-__device__ __forceinline__ void occupations_block(const View& v, const double* __restrict__ f, int nbands, int a, int s) {
+// Eqs. (4), (8), (A2), (B3).  The (k, band) sum of every (atom, spin channel) [collinear] or atom
+// [non-collinear] is split over OCC_SPLIT CTAs.  In a CTA, thread (pair, slice) takes matrix element
+// (a, b) over a strided subset of the CTA's (k, band) range; slices are added in order and the CTA
+// stores its partial.  The CTA that finishes last (a counter per matrix, reset by that CTA) adds the
+// OCC_SPLIT partials in order and writes rho and Pbar, so the result does not depend on scheduling.
+__device__ __forceinline__ void occupations_block(const View& v, const double* __restrict__ f, int nbands, int a, int s,
+                                                  int z) {
     const int M = v.atom_M[a], mo = v.atom_moff[a], sp = v.atom_species[a];
     const int D = v.noncollinear ? 2 * M : M;
     const int P = D * D;
@@ -47,10 +51,13 @@ __device__ __forceinline__ void occupations_block(const View& v, const double* _
     const int pair = threadIdx.x % P, slice = threadIdx.x / P;
     const int ia = pair / D, ib = pair % D;
     __shared__ double2 red_r[CTA], red_p[CTA];
+    __shared__ int s_last;
+    const int total = v.nk * nbands;
+    const int chunk = (total + OCC_SPLIT - 1) / OCC_SPLIT;
+    const int kb0 = z * chunk, kb1 = min(total, kb0 + chunk);
     double2 r = make_double2(0.0, 0.0), pb = make_double2(0.0, 0.0);
     if (slice < SL) {
-        int total = v.nk * nbands;
-        for (int kb = slice; kb < total; kb += SL) {
+        for (int kb = kb0 + slice; kb < kb1; kb += SL) {
             int k = kb / nbands, band = kb % nbands;
             double2 pa, pbv;
             double w, nb;
@@ -76,25 +83,45 @@ __device__ __forceinline__ void occupations_block(const View& v, const double* _
     red_r[threadIdx.x] = r;
     red_p[threadIdx.x] = pb;
     __syncthreads();
+    const int mat = a * 2 + s;
+    double2* part = v.occ_part + ((int64_t)mat * OCC_SPLIT + z) * 2 * OCC_MAXP;
     if (slice == 0 && threadIdx.x < P) {
         for (int q = 1; q < SL; ++q) {
             double2 x = red_r[q * P + pair], y = red_p[q * P + pair];
             r.x += x.x; r.y += x.y; pb.x += y.x; pb.y += y.y;
         }
-        int64_t o = v.atom_mat_off[a] + (int64_t)s * P + pair;
-        v.rho[o] = r;
-        v.pbar[o] = pb;
+        part[pair] = r;
+        part[OCC_MAXP + pair] = pb;
     }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&v.occ_count[mat], 1) == OCC_SPLIT - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x < P) {
+        double2 rr = make_double2(0.0, 0.0), pp = make_double2(0.0, 0.0);
+        for (int q = 0; q < OCC_SPLIT; ++q) {
+            const double2* pq = v.occ_part + ((int64_t)mat * OCC_SPLIT + q) * 2 * OCC_MAXP;
+            double2 x = __ldcg(pq + pair), y = __ldcg(pq + OCC_MAXP + pair);
+            rr.x += x.x; rr.y += x.y; pp.x += y.x; pp.y += y.y;
+        }
+        int64_t o = v.atom_mat_off[a] + (int64_t)s * P + pair;
+        v.rho[o] = rr;
+        v.pbar[o] = pp;
+    }
+    if (threadIdx.x == 0) v.occ_count[mat] = 0;
 }
 
 __global__ void k_occupations(View v, const double* __restrict__ f, int nbands) {
-    occupations_block(v, f, nbands, blockIdx.x, blockIdx.y);
+    occupations_block(v, f, nbands, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 __global__ void k_occupations_batch(const View* __restrict__ views, const ProjArgs* __restrict__ args, const double* const* f) {
     const View& v = views[blockIdx.z];
-    if ((int)blockIdx.x >= v.natoms || (int)blockIdx.y >= (v.noncollinear ? 1 : v.ns)) return;
-    occupations_block(v, f[blockIdx.z], args[blockIdx.z].nbands, blockIdx.x, blockIdx.y);
+    const int s = blockIdx.y / OCC_SPLIT, z = blockIdx.y % OCC_SPLIT;
+    if ((int)blockIdx.x >= v.natoms || s >= (v.noncollinear ? 1 : v.ns)) return;
+    occupations_block(v, f[blockIdx.z], args[blockIdx.z].nbands, blockIdx.x, s, z);
 }
 
 __device__ __forceinline__ double warp_sum(double x) {
@@ -364,7 +391,7 @@ cudaError_t launch_nbar(const View& v, int nbands, cudaStream_t st) {
 }
 
 cudaError_t launch_occupations(const View& v, const double* f, int nbands, cudaStream_t st) {
-    dim3 grid(v.natoms, v.noncollinear ? 1 : v.ns);
+    dim3 grid(v.natoms, v.noncollinear ? 1 : v.ns, OCC_SPLIT);
     k_occupations<<<grid, CTA, 0, st>>>(v, f, nbands);
     return cudaGetLastError();
 }
@@ -379,7 +406,7 @@ cudaError_t launch_occupations_batch(const BatchLaunch& b, cudaStream_t st) {
     k_nbar_batch<<<g1, 256, 0, st>>>(b.views, b.args);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    dim3 g2(b.max_atoms, b.max_ns, b.nsys);
+    dim3 g2(b.max_atoms, b.max_ns * OCC_SPLIT, b.nsys);
     k_occupations_batch<<<g2, CTA, 0, st>>>(b.views, b.args, b.f);
     return cudaGetLastError();
 }
