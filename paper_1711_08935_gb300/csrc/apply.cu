@@ -43,21 +43,6 @@ __device__ __forceinline__ float pow2f(int e) { return e < -126 ? 0.0f : __int_a
 
 __device__ __forceinline__ int exp_field_d(double x) { return (__double2hiint(x) >> 20) & 0x7FF; }
 
-// Split a double with exponent field <= Em into floats hi + lo of x * 2^(1023-Em) (47 significant bits;
-// zeros, denormals and values 2^126 below 2^(Em-1023) flush to zero).  Integer operations only.
-__device__ __forceinline__ void split_scaled_d(double x, int Em, float& hi, float& lo) {
-    unsigned whi = (unsigned)__double2hiint(x), wlo = (unsigned)__double2loint(x);
-    int E = (whi >> 20) & 0x7FF;
-    unsigned sgn = whi & 0x80000000u;
-    unsigned t = __funnelshift_r(wlo, whi, 29);
-    unsigned hb = (t - ((unsigned)(Em - 127) << 23)) | sgn;
-    unsigned ew = ((whi & 0x7FF00000u) << 3) - ((unsigned)(Em - 104) << 23);
-    unsigned f0 = ew | sgn;
-    unsigned f1 = f0 | ((wlo >> 6) & 0x7FFFFFu);
-    hi = (E > 0 && E + 126 >= Em) ? __uint_as_float(hb) : 0.0f;
-    lo = (E > 0 && E + 103 >= Em) ? (__uint_as_float(f1) - __uint_as_float(f0)) : 0.0f;
-}
-
 // Nearest double to (h + l) * 2^sc for a normalised float pair (|l| <= ulp(h)/2), assembled with
 // integer operations: the bit pattern of h as a double plus l counted in units of that double's ulp
 // (half-ulps when h is a power of two and l points toward zero).

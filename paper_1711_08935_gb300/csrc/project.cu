@@ -183,22 +183,19 @@ __device__ __forceinline__ void proj_body_f32(const View& v, const Tile& t, int 
 // ------------------------------------------------------------------------------------------------
 // PAIR policy (complex128 states, FP32-pair arithmetic)
 // ------------------------------------------------------------------------------------------------
-// Split a double with biased exponent field <= Em into float hi + lo of x * 2^(1023-Em).
-// hi = top 24 significant bits, lo = the next 23 (error <= 2^-47 |x|).  Values 2^126 below the
-// chain maximum (and zeros/denormals) are flushed.
+// Split a double with biased exponent field E <= Em (Em >= 127) into floats hi + lo of x * 2^(1023-Em):
+// hi = the top 24 significant bits, lo = the next 23 (error < 2^-46 of 2^(E-Em)).  Both are formed
+// as an exact float mantissa times the signed power of two 2^(E-Em): hi from the top 23 fraction bits
+// under exponent 127, lo from the next 23 bits as (1.f - 1) 2^-23.  Values 2^126 below 2^(Em-1023),
+// zeros and denormals give hi = lo = 0 (Em >= 127 makes the scale of E = 0 vanish).
 __device__ __forceinline__ void split_scaled(double x, int Em, float& hi, float& lo) {
-    unsigned whi = (unsigned)__double2hiint(x), wlo = (unsigned)__double2loint(x);
-    int E = (whi >> 20) & 0x7FF;
-    unsigned sgn = whi & 0x80000000u;
-    unsigned t = __funnelshift_r(wlo, whi, 29);                         // [E8..E0][m51..m29]
-    unsigned hb = (t - ((unsigned)(Em - 127) << 23)) | sgn;
-    bool okh = (E > 0) && (E + 126 >= Em);
-    unsigned ew = ((whi & 0x7FF00000u) << 3) - ((unsigned)(Em - 104) << 23);
-    unsigned f0 = ew | sgn;
-    unsigned f1 = f0 | ((wlo >> 6) & 0x7FFFFFu);
-    bool okl = (E > 0) && (E + 103 >= Em);
-    hi = okh ? __uint_as_float(hb) : 0.0f;
-    lo = okl ? (__uint_as_float(f1) - __uint_as_float(f0)) : 0.0f;
+    const unsigned whi = (unsigned)__double2hiint(x), wlo = (unsigned)__double2loint(x);
+    const unsigned mh = (__funnelshift_l(wlo, whi, 3) & 0x007FFFFFu) | 0x3F800000u;   // 1.f, top 23 fraction bits
+    const unsigned ml = ((wlo >> 6) & 0x007FFFFFu) | 0x3F800000u;                     // 1.g, next 23 bits
+    const int eh = max((int)((whi >> 20) & 0x7FFu) + 127 - Em, 0);                    // exponent of 2^(E-Em)
+    const float sc = __uint_as_float(((unsigned)eh << 23) + (whi & 0x80000000u));   // signed scale, 0 below range
+    hi = __uint_as_float(mh) * sc;
+    lo = __fmaf_rn(__uint_as_float(ml), 0x1p-23f, -0x1p-23f) * sc;
 }
 
 __device__ __forceinline__ int exp_field(double x) { return (__double2hiint(x) >> 20) & 0x7FF; }
@@ -261,6 +258,7 @@ __device__ __forceinline__ void proj_body_pair(const View& v, const Tile& t, int
             for (int c = 0; c < CH; ++c) Ec = max(Ec, max(exp_field(x[c].x), exp_field(x[c].y)));
             if (Ec == 0x7FF) bad = true;
             if (Ec == 0) continue;
+            Ec = max(Ec, 127);   // the split needs Em >= 127 (zeros then scale to 0)
             if (Ec > Em_run) {
                 if (Em_run != 0) {
                     float s = pow2f(Em_run - Ec);
