@@ -62,6 +62,16 @@ __device__ __forceinline__ void write_partial(const View& v, const Tile& t, int 
     v.part[((int64_t)ks * v.max_bands + band) * v.TM + t.moff + m] = r;
 }
 
+// After the butterfly reductions every lane of a band's group holds the same sums, so the FP64
+// epilogue (conversion, Bloch phase, dV) is spread over the lanes, one orbital each: it then issues
+// once per warp instead of once per orbital on this GPU's narrow FP64 pipe.
+template <int M, int Q, typename F>
+__device__ __forceinline__ void per_lane_orbital(int q, F&& body) {
+#pragma unroll
+    for (int m0 = 0; m0 < M; m0 += Q)
+        if (m0 + q < M) body(m0 + q);
+}
+
 // ------------------------------------------------------------------------------------------------
 // F64 policy
 // ------------------------------------------------------------------------------------------------
@@ -114,8 +124,14 @@ __device__ __forceinline__ void proj_body_f64(const View& v, const Tile& t, int 
             acc[m].x += shfl_x(acc[m].x, off);
             acc[m].y += shfl_x(acc[m].y, off);
         }
-    if (row && q == 0)
-        for (int m = 0; m < M; ++m) write_partial(v, t, ks, band, m, acc[m].x, acc[m].y);
+    if (row)
+        per_lane_orbital<M, Q>(q, [&](int mq) {
+            double2 a = acc[0];
+#pragma unroll
+            for (int m = 1; m < M; ++m)
+                if (m == mq) a = acc[m];
+            write_partial(v, t, ks, band, mq, a.x, a.y);
+        });
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -175,9 +191,14 @@ __device__ __forceinline__ void proj_body_f32(const View& v, const Tile& t, int 
                   make_float2(shfl_x(R[m].l.x, off), shfl_x(R[m].l.y, off))};
             df_add(R[m], o);
         }
-    if (row && q == 0)
-        for (int m = 0; m < M; ++m)
-            write_partial(v, t, ks, band, m, (double)R[m].h.x + (double)R[m].l.x, (double)R[m].h.y + (double)R[m].l.y);
+    if (row)
+        per_lane_orbital<M, Q>(q, [&](int mq) {
+            DF2 a = R[0];
+#pragma unroll
+            for (int m = 1; m < M; ++m)
+                if (m == mq) a = R[m];
+            write_partial(v, t, ks, band, mq, (double)a.h.x + (double)a.l.x, (double)a.h.y + (double)a.l.y);
+        });
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -322,15 +343,21 @@ __device__ __forceinline__ void proj_body_pair(const View& v, const Tile& t, int
                   make_float2(shfl_x(R[m].l.x, off), shfl_x(R[m].l.y, off))};
             df_add(R[m], o);
         }
-    unsigned anybad = __any_sync(0xffffffffu, bad);
-    if (row && q == 0) {
-        double sc = ldexp(1.0, Em_max - 1023);
-        for (int m = 0; m < M; ++m) {
-            double re = ((double)R[m].h.x + (double)R[m].l.x) * sc;
-            double im = ((double)R[m].h.y + (double)R[m].l.y) * sc;
+    int anybad = bad ? 1 : 0;   // any non-finite value among this band's lanes
+#pragma unroll
+    for (int off = Q / 2; off > 0; off >>= 1) anybad |= __shfl_xor_sync(0xffffffffu, anybad, off);
+    if (row) {
+        const double sc = ldexp(1.0, Em_max - 1023);
+        per_lane_orbital<M, Q>(q, [&](int mq) {
+            DF2 a = R[0];
+#pragma unroll
+            for (int m = 1; m < M; ++m)
+                if (m == mq) a = R[m];
+            double re = ((double)a.h.x + (double)a.l.x) * sc;
+            double im = ((double)a.h.y + (double)a.l.y) * sc;
             if (anybad) { re = __longlong_as_double(0x7FF8000000000000LL); im = re; }
-            write_partial(v, t, ks, band, m, re, im);
-        }
+            write_partial(v, t, ks, band, mq, re, im);
+        });
     }
 }
 
