@@ -55,11 +55,18 @@ __device__ __forceinline__ float pow2f(int e) {   // 2^e as float for e in [-126
     return e < -126 ? 0.0f : __int_as_float((e + 127) << 23);
 }
 
+// Tile partial sum, before the Bloch phase and dV (k_tile_reduce applies both once per image segment).
 __device__ __forceinline__ void write_partial(const View& v, const Tile& t, int ks, int band, int m, double re, double im) {
-    int k = ks / v.ns;
-    double2 ph = v.seg_phase[t.seg * v.nk + k];
-    double2 r = make_double2(v.dV * (ph.x * re - ph.y * im), v.dV * (ph.x * im + ph.y * re));
-    v.part[((int64_t)ks * v.max_bands + band) * v.TM + t.moff + m] = r;
+    v.part[((int64_t)ks * v.max_bands + band) * v.TM + t.moff + m] = make_double2(re, im);
+}
+
+// Exact float -> double times 2^s with integer operations (the conversion instruction runs on the
+// FP64 pipe).  Zeros and FP32 denormals give 0; s must keep the result normal.
+__device__ __forceinline__ double f2d_scaled(float f, int s) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xFFu;
+    const unsigned hi = (u & 0x80000000u) | ((e + 896u + (unsigned)s) << 20) | ((u & 0x7FFFFFu) >> 3);
+    return e == 0 ? 0.0 : __hiloint2double((int)hi, (int)(u << 29));
 }
 
 // After the butterfly reductions every lane of a band's group holds the same sums, so the FP64
@@ -197,7 +204,7 @@ __device__ __forceinline__ void proj_body_f32(const View& v, const Tile& t, int 
 #pragma unroll
             for (int m = 1; m < M; ++m)
                 if (m == mq) a = R[m];
-            write_partial(v, t, ks, band, mq, (double)a.h.x + (double)a.l.x, (double)a.h.y + (double)a.l.y);
+            write_partial(v, t, ks, band, mq, f2d_scaled(a.h.x, 0) + f2d_scaled(a.l.x, 0), f2d_scaled(a.h.y, 0) + f2d_scaled(a.l.y, 0));
         });
 }
 
@@ -347,14 +354,14 @@ __device__ __forceinline__ void proj_body_pair(const View& v, const Tile& t, int
 #pragma unroll
     for (int off = Q / 2; off > 0; off >>= 1) anybad |= __shfl_xor_sync(0xffffffffu, anybad, off);
     if (row) {
-        const double sc = ldexp(1.0, Em_max - 1023);
+        const int sc = Em_max - 1023;   // the sums are in units of 2^(Em_max - 1023), Em_max >= 127 or sums zero
         per_lane_orbital<M, Q>(q, [&](int mq) {
             DF2 a = R[0];
 #pragma unroll
             for (int m = 1; m < M; ++m)
                 if (m == mq) a = R[m];
-            double re = ((double)a.h.x + (double)a.l.x) * sc;
-            double im = ((double)a.h.y + (double)a.l.y) * sc;
+            double re = f2d_scaled(a.h.x, sc) + f2d_scaled(a.l.x, sc);
+            double im = f2d_scaled(a.h.y, sc) + f2d_scaled(a.l.y, sc);
             if (anybad) { re = __longlong_as_double(0x7FF8000000000000LL); im = re; }
             write_partial(v, t, ks, band, mq, re, im);
         });
@@ -509,12 +516,32 @@ __device__ __forceinline__ void tile_reduce_elem(const View& v, int nbands, int6
     while (a + 1 < v.natoms && v.atom_moff[a + 1] <= j) ++a;
     int m = j - v.atom_moff[a];
     const double2* prow = v.part + ((int64_t)ks * v.max_bands + band) * v.TM;
-    double re = 0.0, im = 0.0;
+    const int k = ks / v.ns;
+    // tiles of one image segment are consecutive: sum them, then apply that segment's Bloch phase
+    double re = 0.0, im = 0.0, sr = 0.0, si = 0.0;
+    int seg = -1;
     for (int t = v.atom_tile_beg[a]; t < v.atom_tile_end[a]; ++t) {
-        double2 x = prow[v.tiles[t].moff + m];
-        re += x.x;
-        im += x.y;
+        const Tile& tl = v.tiles[t];
+        if (tl.seg != seg) {
+            if (seg >= 0) {
+                const double2 ph = v.seg_phase[seg * v.nk + k];
+                re += ph.x * sr - ph.y * si;
+                im += ph.x * si + ph.y * sr;
+            }
+            seg = tl.seg;
+            sr = si = 0.0;
+        }
+        const double2 x = prow[tl.moff + m];
+        sr += x.x;
+        si += x.y;
     }
+    if (seg >= 0) {
+        const double2 ph = v.seg_phase[seg * v.nk + k];
+        re += ph.x * sr - ph.y * si;
+        im += ph.x * si + ph.y * sr;
+    }
+    re *= v.dV;
+    im *= v.dV;
     if (!isfinite(re) || !isfinite(im)) atomicOr(v.status, ST_NONFINITE);
     v.p[((int64_t)ks * v.max_bands + band) * v.MT + j] = make_double2(re, im);
 }
