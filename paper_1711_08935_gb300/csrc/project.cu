@@ -144,13 +144,21 @@ __device__ __forceinline__ void proj_body_f64(const View& v, const Tile& t, int 
 // ------------------------------------------------------------------------------------------------
 // F32 policy (complex64 states)
 // ------------------------------------------------------------------------------------------------
+// Orbital rows of a tile for this policy: per point 2*MP floats, [hi_0 .. hi_{MP-1}, lo_0 .. lo_{MP-1}]
+// with MP = M rounded up to even (zero padding).  Products pair two orbitals against one broadcast
+// state component, (phi_m, phi_m+1) x (x_re, x_re), so one 8-byte shared load feeds two orbitals:
+// half the shared-memory wavefronts of a per-orbital (hi, hi, lo, lo) row, which bound this kernel.
 template <int M, int Q, int CH, int PF, int G>
 __device__ __forceinline__ void proj_body_f32(const View& v, const Tile& t, int ks, int band, const float2* __restrict__ row,
-                                              const int* s_idx, const float4* s_phi, const float4* s_g) {
+                                              const int* s_idx, const float* s_phf, const float4* s_g) {
+    constexpr int MP = (M + 1) & ~1, NP = MP / 2;
     const int q = threadIdx.x & (Q - 1);
-    DF2 R[M];
+    DF2 Rr[NP], Ri[NP];   // running sums of the real and imaginary parts of orbitals (2j, 2j+1)
 #pragma unroll
-    for (int m = 0; m < M; ++m) R[m] = DF2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    for (int j = 0; j < NP; ++j) {
+        Rr[j] = DF2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        Ri[j] = Rr[j];
+    }
     if (row) {
         for (int i0 = q; i0 < t.np; i0 += Q * CH) {
             float2 x[CH];
@@ -173,38 +181,58 @@ __device__ __forceinline__ void proj_body_f32(const View& v, const Tile& t, int 
                     if (i < t.np) prefetch_l2(row + s_idx[i]);
                 }
             }
-            DF2 ch[M];
+            DF2 cr[NP], ci[NP];
 #pragma unroll
-            for (int m = 0; m < M; ++m) ch[m] = DF2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+            for (int j = 0; j < NP; ++j) {
+                cr[j] = DF2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+                ci[j] = cr[j];
+            }
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
-                const float4* ph = s_phi + (i0 + c * Q) * M;
+                const float* ph = s_phf + (i0 + c * Q) * (2 * MP);
+                const float2 xr = make_float2(x[c].x, x[c].x), xi = make_float2(x[c].y, x[c].y);
 #pragma unroll
-                for (int m = 0; m < M; ++m) {
-                    float4 f = ph[m];   // (hi, hi, lo, lo)
-                    ch[m].h = ffma2(make_float2(f.x, f.y), x[c], ch[m].h);
-                    ch[m].l = ffma2(make_float2(f.z, f.w), x[c], ch[m].l);
+                for (int j = 0; j < NP; ++j) {
+                    const float2 h2 = *reinterpret_cast<const float2*>(ph + 2 * j);
+                    const float2 l2 = *reinterpret_cast<const float2*>(ph + MP + 2 * j);
+                    cr[j].h = ffma2(h2, xr, cr[j].h);
+                    ci[j].h = ffma2(h2, xi, ci[j].h);
+                    cr[j].l = ffma2(l2, xr, cr[j].l);
+                    ci[j].l = ffma2(l2, xi, ci[j].l);
                 }
             }
 #pragma unroll
-            for (int m = 0; m < M; ++m) df_add(R[m], ch[m]);
+            for (int j = 0; j < NP; ++j) {
+                df_add(Rr[j], cr[j]);
+                df_add(Ri[j], ci[j]);
+            }
         }
     }
 #pragma unroll
     for (int off = Q / 2; off > 0; off >>= 1)
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-            DF2 o{make_float2(shfl_x(R[m].h.x, off), shfl_x(R[m].h.y, off)),
-                  make_float2(shfl_x(R[m].l.x, off), shfl_x(R[m].l.y, off))};
-            df_add(R[m], o);
+        for (int j = 0; j < NP; ++j) {
+            DF2 o{make_float2(shfl_x(Rr[j].h.x, off), shfl_x(Rr[j].h.y, off)),
+                  make_float2(shfl_x(Rr[j].l.x, off), shfl_x(Rr[j].l.y, off))};
+            df_add(Rr[j], o);
+            DF2 u{make_float2(shfl_x(Ri[j].h.x, off), shfl_x(Ri[j].h.y, off)),
+                  make_float2(shfl_x(Ri[j].l.x, off), shfl_x(Ri[j].l.y, off))};
+            df_add(Ri[j], u);
         }
     if (row)
         per_lane_orbital<M, Q>(q, [&](int mq) {
-            DF2 a = R[0];
+            float rh = Rr[0].h.x, rl = Rr[0].l.x, ih = Ri[0].h.x, il = Ri[0].l.x;
 #pragma unroll
             for (int m = 1; m < M; ++m)
-                if (m == mq) a = R[m];
-            write_partial(v, t, ks, band, mq, f2d_scaled(a.h.x, 0) + f2d_scaled(a.l.x, 0), f2d_scaled(a.h.y, 0) + f2d_scaled(a.l.y, 0));
+                if (m == mq) {
+                    const DF2& a = Rr[m / 2];
+                    const DF2& b = Ri[m / 2];
+                    rh = (m & 1) ? a.h.y : a.h.x;
+                    rl = (m & 1) ? a.l.y : a.l.x;
+                    ih = (m & 1) ? b.h.y : b.h.x;
+                    il = (m & 1) ? b.l.y : b.l.x;
+                }
+            write_partial(v, t, ks, band, mq, f2d_scaled(rh, 0) + f2d_scaled(rl, 0), f2d_scaled(ih, 0) + f2d_scaled(il, 0));
         });
 }
 
@@ -392,6 +420,16 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
         double* s_phi = reinterpret_cast<double*>(smem + TILE * sizeof(int));
         for (int e = threadIdx.x; e < TILE * t.M; e += CTA)
             s_phi[e] = (e < t.np * t.M) ? v.phi64[t.phi0 + e] : 0.0;
+    } else if (POL == P_F32) {
+        float* s_phf = reinterpret_cast<float*>(smem + TILE * sizeof(int));
+        const int MP = (t.M + 1) & ~1;
+        for (int e = threadIdx.x; e < TILE_PAD * MP; e += CTA) {
+            const int i = e / MP, m = e - i * MP;
+            float hi = 0.f, lo = 0.f;
+            if (i < t.np && m < t.M) { hi = v.phi_hi[t.phi0 + (int64_t)i * t.M + m]; lo = v.phi_lo[t.phi0 + (int64_t)i * t.M + m]; }
+            s_phf[i * 2 * MP + m] = hi;
+            s_phf[i * 2 * MP + MP + m] = lo;
+        }
     } else {
         float4* s_phi = reinterpret_cast<float4*>(smem + TILE * sizeof(int));
         int pe = -200;
@@ -444,14 +482,14 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
                 default: proj_body_pair<7, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phi, pe, s_g); break;
             }
         } else {
-            const float4* s_phi = reinterpret_cast<const float4*>(smem + TILE * sizeof(int));
+            const float* s_phf = reinterpret_cast<const float*>(smem + TILE * sizeof(int));
             const float2* row = active ? reinterpret_cast<const float2*>(a.psi) + off : nullptr;
             const float4* s_g = reinterpret_cast<const float4*>(s_gauge);
             switch (t.M) {
-                case 1: proj_body_f32<1, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phi, s_g); break;
-                case 3: proj_body_f32<3, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phi, s_g); break;
-                case 5: proj_body_f32<5, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phi, s_g); break;
-                default: proj_body_f32<7, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phi, s_g); break;
+                case 1: proj_body_f32<1, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phf, s_g); break;
+                case 3: proj_body_f32<3, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phf, s_g); break;
+                case 5: proj_body_f32<5, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phf, s_g); break;
+                default: proj_body_f32<7, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phf, s_g); break;
             }
         }
     }
