@@ -409,6 +409,11 @@ def run_rt(args):
     h = dftu.handle_for_system(s, nb)
     _coulomb_all(h, s)
     work = torch.zeros_like(psi)
+    # kernel shapes tuned on these states; the tuner's applies go into `work`, which every Taylor step
+    # assigns before it reads it
+    from paper_1711_08935_gb300.autotune import autotune
+    h.project(psi); h.occupations(f); h.acbn0_uj()
+    tuned = autotune(h, psi, out=work)
     n0 = (psi.abs() ** 2).sum(-1).double() * s.grid.dV
     dt = 0.01
     side = torch.cuda.Stream()
@@ -446,7 +451,7 @@ def run_rt(args):
         "steps_per_s": round(1e3 / ms, 2), "graph_ms_total": round(ms * args.rt_steps, 2),
         "norm_drift_max": float((n1 - n0).abs().max()), "state_generation_s": round(gen_s, 1),
         "peak": peak, "peak_source": src, "frac_of_peak": round(step_bytes / (ms * 1e-3) / 1e9 / peak, 4), "clocks": clk,
-        "U_eV_first_atoms": [round(x * dftu.HARTREE_EV, 5) for x in h.results()["U"][:6]]}))
+        "U_eV_first_atoms": [round(x * dftu.HARTREE_EV, 5) for x in h.results()["U"][:6]], "tuning": tuned}))
 
 
 def run_molecules(args):
