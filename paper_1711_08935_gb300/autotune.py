@@ -43,3 +43,25 @@ def autotune(h: dftu.Handle, psi: torch.Tensor, reps: int = 3, out: torch.Tensor
         out[kind] = {"variant": best, "ms": [round(t, 4) for t in times]}
     h.project(psi)      # leave fresh projections of the current states in the handle
     return out
+
+
+def autotune_batch(batch: dftu.Batch, dtype: torch.dtype, coef: torch.Tensor = None, reps: int = 3) -> dict:
+    """The same for a batch: its persistent launches use the shapes set on its first member, so every
+    shape is timed on the batch's own launches.  The batch must hold potentials (batch acbn0_uj) for
+    the apply to run; its applies change the bound states, with `coef` as the coefficient."""
+    h0 = batch.handles[0]
+    stream = torch.cuda.current_stream(torch.device("cuda", batch.device))
+    out = {}
+    for kind in ("project", "apply"):
+        which = WHICH[(kind, dtype)]
+        n = h0.lib.dftu_kernel_variants(which)
+        times = []
+        for v in range(n):
+            h0.set_kernel_variant(which, v)
+            fn = batch.project if kind == "project" else (lambda: batch.apply(coef))
+            times.append(_time(fn, reps, stream))
+        best = min(range(n), key=lambda i: times[i])
+        h0.set_kernel_variant(which, best)
+        out[kind] = {"variant": best, "ms": [round(t, 4) for t in times]}
+    batch.project()
+    return out
