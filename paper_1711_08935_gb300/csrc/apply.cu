@@ -432,9 +432,9 @@ cudaError_t launch_apply(const View& v, void* psi, dftu_prec prec, dftu_f64_mode
                          const std::vector<int>& color_beg, int variant, int accumulate, cudaStream_t st, bool gauge) {
     ApplyArgs a{psi, sk, ss, sn, nbands, coef, nullptr, accumulate};
     if (gauge) {   // one shape per arithmetic policy with the gauge phases (Sec. V)
-        if (prec == DFTU_C64) return run_apply<A_F32, 8, 4, 8, 0, 1>(v, a, color_order, color_beg, st);
+        if (prec == DFTU_C64) return run_apply<A_F32, 8, 4, 8, 1, 1>(v, a, color_order, color_beg, st);
         if (mode == DFTU_F64_NATIVE) return run_apply<A_F64, 8, 4, 4, 0, 1>(v, a, color_order, color_beg, st);
-        return run_apply<A_PAIR, 8, 4, 4, 0, 1>(v, a, color_order, color_beg, st);
+        return run_apply<A_PAIR, 8, 4, 4, 1, 1>(v, a, color_order, color_beg, st);
     }
     if (prec == DFTU_C64) {
         switch (variant) {   // (lanes per band, band groups per CTA, points in flight per lane)

@@ -614,7 +614,7 @@ cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_
     if (gauge) {   // one shape per arithmetic policy with the gauge phases (Sec. V)
         if (prec == DFTU_C64) e = run_project<P_F32, 8, 16, 4, 0, 2, 1>(v, a, st);
         else if (mode == DFTU_F64_NATIVE) e = run_project<P_F64, 8, 1, 4, 0, 2, 1>(v, a, st);
-        else e = run_project<P_PAIR, 8, 8, 4, 0, 2, 1>(v, a, st);
+        else e = run_project<P_PAIR, 4, 8, 4, 1, 2, 1>(v, a, st);
     } else if (prec == DFTU_C64) {
         switch (variant) {   // (lanes per band, points per chain, band groups per CTA)
             case 1: e = run_project<P_F32, 8, 8, 4, 0>(v, a, st); break;
