@@ -1,12 +1,12 @@
 // Sphere gather + projection p = dV sum_j phi_m(j) exp(+i k.T_j) psi(idx_j)   (inside Eqs. 4 and 6).
 //
 // Work decomposition: one CTA per (tile, band chunk, k*spin).  A tile holds up to TILE points of one
-// (atom, lattice image) segment, so its Bloch phase is a single number applied to the tile sum.  The
-// CTA stages the tile's grid indices and orbital values in shared memory once and streams the
-// bands of its chunk: Q adjacent lanes walk the points of one band (Q*16 or Q*8 contiguous bytes
-// per band row when the points run along x), 32/Q bands per warp.  Partial sums per tile are
-// written in FP64 and summed over the tiles of each atom in a fixed order by k_tile_reduce, so
-// results are deterministic.
+// (atom, lattice image) segment, so its Bloch phase is a single number.  The CTA stages the tile's
+// grid indices and orbital values in shared memory once and streams the bands of its chunk: Q
+// adjacent lanes walk the points of one band (Q*16 or Q*8 contiguous bytes per band row when the
+// points run along x), 32/Q bands per warp.  Partial sums per tile are written in FP64 without the
+// phase; k_tile_reduce sums the tiles of each atom in a fixed order, applies each image segment's
+// phase once and scales by dV, so results are deterministic.
 //
 // Arithmetic policies
 //   F64  : complex128 states, FP64 FMAs (the FP64 pipe of this GPU runs at ~1/70 of FP32).
@@ -15,8 +15,8 @@
 //          into an accumulator offset by a power of two C >= 4*sum|terms| so that the running sum
 //          moves in one binade: t = s - acc is exact and the rounding residual a*b - t is caught
 //          in a second float.  Chains are merged with TwoSum.  Accuracy ~2^-44 of the chain scale.
-//   F32  : complex64 states, FP32 orbitals hi + lo, FP32 chunk sums merged with TwoSum per lane,
-//          FP64 across tiles.
+//   F32  : complex64 states, FP32 orbitals hi + lo paired two orbitals at a time, FP32 chunk sums
+//          merged with TwoSum per lane, FP64 across tiles.
 #include <algorithm>
 #include <mutex>
 #include <utility>
