@@ -254,6 +254,7 @@ def run_ours(args):
                    "sphere_points": int(sum(npts)), "bands": nb, "kpoints": s.nk, "spins": 2},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_source": peak_src,
+                     "frac_of_nominal_7900": round(achieved / 7900.0, 4),
                      "traffic": round(traffic) if traffic else None,
                      "bytes_per_launch": dom_bytes},
         "kernels_ms": {"project": round(proj64, 4), "occupations+acbn0": round(small64, 4), "apply": round(app64, 4),
