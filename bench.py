@@ -693,7 +693,7 @@ def run_gauge(args):
         "kernels_ms": {"project_gauge": round(pr_g, 4), "apply_gauge": round(ap_g, 4), "project_plain": round(pr_plain, 4),
                        "apply_plain": round(ap_plain, 4)},
         "plain_pass_ms": round(ms_plain, 4), "gauge_overhead": round(ms_g / ms_plain, 3),
-        "current": {"ms": round(cur_ms, 3), "J": [float(x) for x in J], "note": "3 projections + contraction + host copy, blocking"},
+        "current": {"ms": round(cur_ms, 3), "J": [float(x) for x in J], "note": "one launch projecting onto the three displaced-orbital tables + contraction + host copy, blocking"},
         "fp32_state": {"ms_per_step": round(ms_g32, 4), "project_ms": round(pr_g32, 4), "apply_ms": round(ap_g32, 4)},
         "tuning": tuned, "gpu_launches": (1 + 2 + 2 + 1 + 1) * args.steps, "device_status": int(status), "clocks": clk}))
 

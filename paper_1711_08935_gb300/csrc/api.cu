@@ -425,7 +425,8 @@ dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, 
     if (e == cudaSuccess) e = dalloc(c, &v.phi_hi, (size_t)phi_off);
     if (e == cudaSuccess) e = dalloc(c, &v.phi_lo, (size_t)phi_off);
     if (e == cudaSuccess) e = dalloc(c, &v.p, (size_t)rowsP * c->max_bands * MT);
-    if (e == cudaSuccess) e = dalloc(c, &v.part, (size_t)rowsP * c->max_bands * TM);
+    v.part_dir_stride = (int64_t)rowsP * c->max_bands * TM;   // three slices: the current's three directions
+    if (e == cudaSuccess) e = dalloc(c, &v.part, (size_t)3 * v.part_dir_stride);
     if (e == cudaSuccess) e = dalloc(c, &v.pgrad, (size_t)3 * rowsP * c->max_bands * MT);
     if (e == cudaSuccess) e = dalloc(c, &c->d_forces, (size_t)3 * natoms);
     if (e == cudaSuccess) e = dalloc(c, &c->d_current, (size_t)3 * natoms);
@@ -756,15 +757,12 @@ dftu_status dftu_hubbard_current(dftu_handle h, const void* psi, dftu_prec prec,
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (!gpu_addressable(c->device, psi, st)) return fail(c, DFTU_ERR_INVALID_ARG, "hubbard_current: the states are not addressable by this GPU (device memory of another GPU, or pageable host memory on a device without pageable access)");
     const int64_t gstride = (int64_t)c->nk * c->ns * c->max_bands * c->MT;
-    cudaError_t e = cudaSuccess;
-    for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
-        View vq = c->v;   // the same states projected onto phi_m d_a, into the gradient buffer
-        vq.phi64 = c->v.phid64 + a * c->phi_total;
-        vq.phi_hi = c->v.phid_hi + a * c->phi_total;
-        vq.phi_lo = c->v.phid_lo + a * c->phi_total;
-        vq.p = c->v.pgrad + a * gstride;
-        e = launch_project(vq, psi, prec, c->f64_mode, nbands, sk, ss, sn, c->variant[prec == DFTU_C64 ? 1 : 0], st, c->gauge_on);
-    }
+    View vq = c->v;   // the same states projected onto phi_m d_a (a = x, y, z) in one launch, into the gradient buffer
+    vq.phi64 = c->v.phid64;
+    vq.phi_hi = c->v.phid_hi;
+    vq.phi_lo = c->v.phid_lo;
+    vq.phi_dir_stride = c->phi_total;
+    cudaError_t e = launch_project_dirs(vq, psi, prec, c->f64_mode, nbands, sk, ss, sn, c->gauge_on, c->v.pgrad, gstride, st);
     if (e == cudaSuccess) e = launch_current(c->v, f, nbands, c->d_current, st);
     const int na = (int)c->atoms.size();
     std::vector<double> Jat(3 * (size_t)na);

@@ -80,7 +80,9 @@ struct View {
 
     double2* p;            // [nk*ns][max_bands][MT]
     double2* pgrad;        // [3][nk*ns][max_bands][MT] projections of the state gradients (forces)
-    double2* part;         // [nk*ns][max_bands][TM]
+    double2* part;         // [3][nk*ns][max_bands][TM]: one slice per direction of a three-table projection
+    int64_t phi_dir_stride;    // elements between the orbital tables of successive directions (0: one table)
+    int64_t part_dir_stride;   // elements between the partial-sum slices of successive directions
     double* nbar;          // collinear [nk*ns][max_bands][nspecies]; non-collinear [nk][max_bands][nspecies]
     double2* rho;          // per atom: collinear [ns][M][M]; non-collinear [2M][2M]   (rho = n^T)
     double2* pbar;         // same layout, renormalised (Eq. 8), transposed like rho
@@ -182,6 +184,12 @@ cudaError_t launch_apply(const View& v, void* psi, dftu_prec prec, dftu_f64_mode
                          const std::vector<int>& color_beg, int variant, int accumulate, cudaStream_t st,
                          bool gauge = false);
 cudaError_t launch_gauge_phases(const View& v, const double* A, cudaStream_t st);
+// Projections onto three orbital tables (v.phi* + a * v.phi_dir_stride, a = 0..2) in one launch, the
+// directions interleaved per tile so that the three reads of a tile's states share L2; results go to
+// p_out + a * p_stride.
+cudaError_t launch_project_dirs(const View& v, const void* psi, dftu_prec prec, dftu_f64_mode mode, int nbands,
+                                int64_t sk, int64_t ss, int64_t sn, bool gauge, double2* p_out, int64_t p_stride,
+                                cudaStream_t st);
 cudaError_t launch_displaced_orbitals(const View& v, int64_t phi_total, cudaStream_t st);
 cudaError_t launch_current(const View& v, const double* f, int nbands, double* Jat, cudaStream_t st);
 cudaError_t launch_taylor_coefs(double dt, int order, double* coefs, cudaStream_t st);

@@ -56,8 +56,10 @@ __device__ __forceinline__ float pow2f(int e) {   // 2^e as float for e in [-126
 }
 
 // Tile partial sum, before the Bloch phase and dV (k_tile_reduce applies both once per image segment).
-__device__ __forceinline__ void write_partial(const View& v, const Tile& t, int ks, int band, int m, double re, double im) {
-    v.part[((int64_t)ks * v.max_bands + band) * v.TM + t.moff + m] = make_double2(re, im);
+// poff: offset of the direction's slice (three-table projections), 0 otherwise.
+__device__ __forceinline__ void write_partial(const View& v, const Tile& t, int ks, int band, int m, double re, double im,
+                                              int64_t poff) {
+    v.part[poff + ((int64_t)ks * v.max_bands + band) * v.TM + t.moff + m] = make_double2(re, im);
 }
 
 // Exact float -> double times 2^s with integer operations (the conversion instruction runs on the
@@ -89,7 +91,7 @@ __device__ __forceinline__ double2 crot(double2 x, double2 g) {
 
 template <int M, int Q, int G>
 __device__ __forceinline__ void proj_body_f64(const View& v, const Tile& t, int ks, int band, const double2* __restrict__ row,
-                                              const int* s_idx, const double* s_phi, const double2* s_g) {
+                                              const int* s_idx, const double* s_phi, const double2* s_g, int64_t poff) {
     const int q = threadIdx.x & (Q - 1);
     double2 acc[M];
 #pragma unroll
@@ -137,7 +139,7 @@ __device__ __forceinline__ void proj_body_f64(const View& v, const Tile& t, int 
 #pragma unroll
             for (int m = 1; m < M; ++m)
                 if (m == mq) a = acc[m];
-            write_partial(v, t, ks, band, mq, a.x, a.y);
+            write_partial(v, t, ks, band, mq, a.x, a.y, poff);
         });
 }
 
@@ -150,7 +152,7 @@ __device__ __forceinline__ void proj_body_f64(const View& v, const Tile& t, int 
 // half the shared-memory wavefronts of a per-orbital (hi, hi, lo, lo) row, which bound this kernel.
 template <int M, int Q, int CH, int PF, int G>
 __device__ __forceinline__ void proj_body_f32(const View& v, const Tile& t, int ks, int band, const float2* __restrict__ row,
-                                              const int* s_idx, const float* s_phf, const float4* s_g) {
+                                              const int* s_idx, const float* s_phf, const float4* s_g, int64_t poff) {
     constexpr int MP = (M + 1) & ~1, NP = MP / 2;
     const int q = threadIdx.x & (Q - 1);
     DF2 Rr[NP], Ri[NP];   // running sums of the real and imaginary parts of orbitals (2j, 2j+1)
@@ -232,7 +234,7 @@ __device__ __forceinline__ void proj_body_f32(const View& v, const Tile& t, int 
                     ih = (m & 1) ? b.h.y : b.h.x;
                     il = (m & 1) ? b.l.y : b.l.x;
                 }
-            write_partial(v, t, ks, band, mq, f2d_scaled(rh, 0) + f2d_scaled(rl, 0), f2d_scaled(ih, 0) + f2d_scaled(il, 0));
+            write_partial(v, t, ks, band, mq, f2d_scaled(rh, 0) + f2d_scaled(rl, 0), f2d_scaled(ih, 0) + f2d_scaled(il, 0), poff);
         });
 }
 
@@ -281,7 +283,7 @@ __device__ __forceinline__ void rot_pair(float2& bh, float2& bl, float4 g) {
 
 template <int M, int Q, int CH, int PF, int G>
 __device__ __forceinline__ void proj_body_pair(const View& v, const Tile& t, int ks, int band, const double2* __restrict__ row,
-                                               const int* s_idx, const float4* s_phi, int pe, const float4* s_g) {
+                                               const int* s_idx, const float4* s_phi, int pe, const float4* s_g, int64_t poff) {
     const int q = threadIdx.x & (Q - 1);
     DF2 R[M];
 #pragma unroll
@@ -391,7 +393,7 @@ __device__ __forceinline__ void proj_body_pair(const View& v, const Tile& t, int
             double re = f2d_scaled(a.h.x, sc) + f2d_scaled(a.l.x, sc);
             double im = f2d_scaled(a.h.y, sc) + f2d_scaled(a.l.y, sc);
             if (anybad) { re = __longlong_as_double(0x7FF8000000000000LL); im = re; }
-            write_partial(v, t, ks, band, mq, re, im);
+            write_partial(v, t, ks, band, mq, re, im, poff);
         });
     }
 }
@@ -402,12 +404,15 @@ __device__ __forceinline__ void proj_body_pair(const View& v, const Tile& t, int
 enum Pol { P_F64 = 0, P_PAIR = 1, P_F32 = 2 };
 
 // One work item: tile `tile_id` of the system described by (v, a), spin/component index ks, every band of
-// band chunk `chunk` (NBG groups of BPC bands).  The tile is staged in shared memory once.
+// band chunk `chunk` (NBG groups of BPC bands), against orbital table `dir` (0 unless the launch projects
+// onto several tables).  The tile is staged in shared memory once.
 template <int POL, int Q, int CH, int NBG, int PF, int G>
 __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, int tile_id, int ks, int chunk,
-                                             unsigned char* smem, int* s_pe) {
+                                             unsigned char* smem, int* s_pe, int dir = 0) {
     int* s_idx = reinterpret_cast<int*>(smem);
     const Tile t = v.tiles[tile_id];
+    const int64_t ph0 = t.phi0 + dir * v.phi_dir_stride;   // this table's rows of the tile
+    const int64_t poff = dir * v.part_dir_stride;
     const int k = ks / v.ns, s = ks % v.ns;
     constexpr int BPW = 32 / Q;
     constexpr int BPC = (CTA / 32) * BPW;
@@ -419,14 +424,14 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
     if (POL == P_F64) {
         double* s_phi = reinterpret_cast<double*>(smem + TILE * sizeof(int));
         for (int e = threadIdx.x; e < TILE * t.M; e += CTA)
-            s_phi[e] = (e < t.np * t.M) ? v.phi64[t.phi0 + e] : 0.0;
+            s_phi[e] = (e < t.np * t.M) ? v.phi64[ph0 + e] : 0.0;
     } else if (POL == P_F32) {
         float* s_phf = reinterpret_cast<float*>(smem + TILE * sizeof(int));
         const int MP = (t.M + 1) & ~1;
         for (int e = threadIdx.x; e < TILE_PAD * MP; e += CTA) {
             const int i = e / MP, m = e - i * MP;
             float hi = 0.f, lo = 0.f;
-            if (i < t.np && m < t.M) { hi = v.phi_hi[t.phi0 + (int64_t)i * t.M + m]; lo = v.phi_lo[t.phi0 + (int64_t)i * t.M + m]; }
+            if (i < t.np && m < t.M) { hi = v.phi_hi[ph0 + (int64_t)i * t.M + m]; lo = v.phi_lo[ph0 + (int64_t)i * t.M + m]; }
             s_phf[i * 2 * MP + m] = hi;
             s_phf[i * 2 * MP + MP + m] = lo;
         }
@@ -435,7 +440,7 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
         int pe = -200;
         for (int e = threadIdx.x; e < TILE_PAD * t.M; e += CTA) {
             float hi = 0.f, lo = 0.f;
-            if (e < t.np * t.M) { hi = v.phi_hi[t.phi0 + e]; lo = v.phi_lo[t.phi0 + e]; }
+            if (e < t.np * t.M) { hi = v.phi_hi[ph0 + e]; lo = v.phi_lo[ph0 + e]; }
             s_phi[e] = make_float4(hi, hi, lo, lo);
             if (hi != 0.f) pe = max(pe, ((__float_as_int(hi) >> 23) & 0xFF) - 127 + 1);   // |hi| < 2^pe
         }
@@ -465,10 +470,10 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
             const double2* row = active ? reinterpret_cast<const double2*>(a.psi) + off : nullptr;
             const double2* s_g = reinterpret_cast<const double2*>(s_gauge);
             switch (t.M) {
-                case 1: proj_body_f64<1, Q, G>(v, t, ks, band, row, s_idx, s_phi, s_g); break;
-                case 3: proj_body_f64<3, Q, G>(v, t, ks, band, row, s_idx, s_phi, s_g); break;
-                case 5: proj_body_f64<5, Q, G>(v, t, ks, band, row, s_idx, s_phi, s_g); break;
-                default: proj_body_f64<7, Q, G>(v, t, ks, band, row, s_idx, s_phi, s_g); break;
+                case 1: proj_body_f64<1, Q, G>(v, t, ks, band, row, s_idx, s_phi, s_g, poff); break;
+                case 3: proj_body_f64<3, Q, G>(v, t, ks, band, row, s_idx, s_phi, s_g, poff); break;
+                case 5: proj_body_f64<5, Q, G>(v, t, ks, band, row, s_idx, s_phi, s_g, poff); break;
+                default: proj_body_f64<7, Q, G>(v, t, ks, band, row, s_idx, s_phi, s_g, poff); break;
             }
         } else if (POL == P_PAIR) {
             const float4* s_phi = reinterpret_cast<const float4*>(smem + TILE * sizeof(int));
@@ -476,30 +481,34 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
             const int pe = *s_pe;
             const float4* s_g = reinterpret_cast<const float4*>(s_gauge);
             switch (t.M) {
-                case 1: proj_body_pair<1, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phi, pe, s_g); break;
-                case 3: proj_body_pair<3, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phi, pe, s_g); break;
-                case 5: proj_body_pair<5, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phi, pe, s_g); break;
-                default: proj_body_pair<7, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phi, pe, s_g); break;
+                case 1: proj_body_pair<1, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phi, pe, s_g, poff); break;
+                case 3: proj_body_pair<3, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phi, pe, s_g, poff); break;
+                case 5: proj_body_pair<5, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phi, pe, s_g, poff); break;
+                default: proj_body_pair<7, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phi, pe, s_g, poff); break;
             }
         } else {
             const float* s_phf = reinterpret_cast<const float*>(smem + TILE * sizeof(int));
             const float2* row = active ? reinterpret_cast<const float2*>(a.psi) + off : nullptr;
             const float4* s_g = reinterpret_cast<const float4*>(s_gauge);
             switch (t.M) {
-                case 1: proj_body_f32<1, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phf, s_g); break;
-                case 3: proj_body_f32<3, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phf, s_g); break;
-                case 5: proj_body_f32<5, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phf, s_g); break;
-                default: proj_body_f32<7, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phf, s_g); break;
+                case 1: proj_body_f32<1, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phf, s_g, poff); break;
+                case 3: proj_body_f32<3, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phf, s_g, poff); break;
+                case 5: proj_body_f32<5, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phf, s_g, poff); break;
+                default: proj_body_f32<7, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phf, s_g, poff); break;
             }
         }
     }
 }
 
-template <int POL, int Q, int CH, int NBG, int PF, int MINB, int G>
+// NDIR > 1: blockIdx.x = tile * NDIR + direction, so the CTAs of one tile and band chunk for the
+// NDIR orbital tables are neighbours in the launch and read the same states while they sit in L2.
+template <int POL, int Q, int CH, int NBG, int PF, int MINB, int G, int NDIR = 1>
 __global__ void __launch_bounds__(CTA, MINB) k_project(View v, ProjArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_pe;
-    project_item<POL, Q, CH, NBG, PF, G>(v, a, blockIdx.x, blockIdx.z, blockIdx.y, smem, &s_pe);
+    const int tile = (NDIR == 1) ? (int)blockIdx.x : (int)blockIdx.x / NDIR;
+    const int dir = (NDIR == 1) ? 0 : (int)blockIdx.x % NDIR;
+    project_item<POL, Q, CH, NBG, PF, G>(v, a, tile, blockIdx.z, blockIdx.y, smem, &s_pe, dir);
 }
 
 // Persistent form over many systems: every CTA takes (system, tile, k*spin) items from a counter until
@@ -592,17 +601,17 @@ __global__ void k_tile_reduce_batch(const View* __restrict__ views, const ProjAr
     tile_reduce_elem(views[blockIdx.y], args[blockIdx.y].nbands, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-template <int POL, int Q, int CH, int NBG, int PF, int MINB = 2, int G = 0>
+template <int POL, int Q, int CH, int NBG, int PF, int MINB = 2, int G = 0, int NDIR = 1>
 static cudaError_t run_project(const View& v, const ProjArgs& a, cudaStream_t st) {
     static_assert(Q * CH <= TILE_PAD - TILE, "chained loops read up to Q*CH rows past the tile");
     size_t smem = TILE * sizeof(int) + (size_t)TILE_PAD * v.maxM * (POL == P_F64 ? sizeof(double) : sizeof(float4)) +
                   (G ? (size_t)TILE_PAD * 16 : 0);
-    auto fn = k_project<POL, Q, CH, NBG, PF, MINB, G>;
+    auto fn = k_project<POL, Q, CH, NBG, PF, MINB, G, NDIR>;
     cudaError_t e = cudaSuccess;
     if (!smem_configured((const void*)fn, (int)smem)) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     constexpr int BPC = (CTA / 32) * (32 / Q);
-    dim3 grid(v.ntiles, (a.nbands + BPC * NBG - 1) / (BPC * NBG), v.nk * v.ns);
+    dim3 grid(v.ntiles * NDIR, (a.nbands + BPC * NBG - 1) / (BPC * NBG), v.nk * v.ns);
     fn<<<grid, CTA, smem, st>>>(v, a);
     return cudaGetLastError();
 }
@@ -644,6 +653,28 @@ cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_
     int64_t n = (int64_t)v.nk * v.ns * nbands * v.MT;
     k_tile_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(v, nbands);
     return cudaGetLastError();
+}
+
+cudaError_t launch_project_dirs(const View& v, const void* psi, dftu_prec prec, dftu_f64_mode mode, int nbands,
+                                int64_t sk, int64_t ss, int64_t sn, bool gauge, double2* p_out, int64_t p_stride,
+                                cudaStream_t st) {
+    ProjArgs a{psi, sk, ss, sn, nbands};
+    cudaError_t e;
+    // the fixed shapes of the gauge path, with and without the phases
+    if (prec == DFTU_C64) e = gauge ? run_project<P_F32, 8, 16, 4, 0, 2, 1, 3>(v, a, st) : run_project<P_F32, 8, 16, 4, 0, 2, 0, 3>(v, a, st);
+    else if (mode == DFTU_F64_NATIVE) e = gauge ? run_project<P_F64, 8, 1, 4, 0, 2, 1, 3>(v, a, st) : run_project<P_F64, 8, 1, 4, 0, 2, 0, 3>(v, a, st);
+    else e = gauge ? run_project<P_PAIR, 4, 8, 4, 1, 2, 1, 3>(v, a, st) : run_project<P_PAIR, 4, 8, 4, 1, 2, 0, 3>(v, a, st);
+    if (e != cudaSuccess) return e;
+    int64_t n = (int64_t)v.nk * v.ns * nbands * v.MT;
+    for (int d = 0; d < 3; ++d) {
+        View vd = v;
+        vd.part = v.part + d * v.part_dir_stride;
+        vd.p = p_out + d * p_stride;
+        k_tile_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(vd, nbands);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <int POL, int Q, int CH, int NBG, int PF, int MINB = 2>
