@@ -258,7 +258,9 @@ dftu_status dftu_project_sphere_noalloc(const void* psi, dftu_prec prec, int nba
  * per-system steps (Nbar, occupations, U/J, potential) run as single batched launches.  Results are
  * read per member with the handle calls above (dftu_get_results etc.); the arithmetic is that of the
  * single-system calls, in the same order per member.  The paper has no counterpart for the batching;
- * it packages Eqs. (4)-(11) for many systems at once. */
+ * it packages Eqs. (4)-(11) for many systems at once.  All members must use the same FP64 mode and
+ * have no vector potential set (dftu_set_vector_potential); otherwise dftu_batch_project and
+ * dftu_batch_apply return DFTU_ERR_INVALID_ARG. */
 typedef struct dftu_batch_ctx* dftu_batch;
 
 /* systems: host array of nsys set-up handles (not owned; they must outlive the batch). */

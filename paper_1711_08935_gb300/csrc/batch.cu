@@ -162,9 +162,25 @@ dftu_status dftu_batch_bind(dftu_batch b, const void* const* psi, dftu_prec prec
     return DFTU_OK;
 }
 
+// The batched kernels run one arithmetic for all members and no gauge phases: members must agree.
+static dftu_status members_uniform(dftu_batch b, const char* what) {
+    const Ctx* c0 = b->members[0];
+    for (size_t s = 0; s < b->members.size(); ++s) {
+        const Ctx* c = b->members[s];
+        if (c->gauge_on)
+            return bfail(b, DFTU_ERR_INVALID_ARG, std::string(what) + ": member " + std::to_string(s) +
+                                                      " has a vector potential set; batches run the plain operator");
+        if (c->f64_mode != c0->f64_mode)
+            return bfail(b, DFTU_ERR_INVALID_ARG, std::string(what) + ": member " + std::to_string(s) +
+                                                      " uses another FP64 mode than member 0");
+    }
+    return DFTU_OK;
+}
+
 dftu_status dftu_batch_project(dftu_batch b, dftu_stream stream) {
     if (!b) return DFTU_ERR_INVALID_ARG;
     if (!b->bound) return bfail(b, DFTU_ERR_NOT_READY, "batch_project: call dftu_batch_bind first");
+    if (dftu_status u = members_uniform(b, "batch_project")) return u;
     Ctx* c0 = b->members[0];
     int prev = -1;
     cudaGetDevice(&prev);
@@ -216,6 +232,8 @@ dftu_status dftu_batch_acbn0_uj(dftu_batch b, dftu_stream stream) {
 
 dftu_status dftu_batch_apply(dftu_batch b, const double* coef, int accumulate, dftu_stream stream) {
     if (!b) return DFTU_ERR_INVALID_ARG;
+    if (!b->bound) return bfail(b, DFTU_ERR_NOT_READY, "batch_apply: call dftu_batch_bind first");
+    if (dftu_status u = members_uniform(b, "batch_apply")) return u;
     for (auto* c : b->members)
         if (!c->pot_ready) return bfail(b, DFTU_ERR_NOT_READY, "batch_apply: call dftu_batch_acbn0_uj first");
     Ctx* c0 = b->members[0];

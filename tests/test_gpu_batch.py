@@ -76,3 +76,37 @@ def test_batch_member_matches_oracle():
     got = ps[2].cpu().numpy()
     assert np.max(np.abs(got - ref["psi_out"])) < 1e-12 * np.max(np.abs(ref["psi_out"]))
     batch.close()
+
+
+def test_batch_refuses_members_it_cannot_run_uniformly():
+    """The batched kernels run one FP64 mode and no gauge phases for all members: a member with a
+    vector potential or another FP64 mode is refused (DFTU_ERR_INVALID_ARG), as is an apply before bind."""
+    dev = torch.device("cuda:0")
+    mem = _members(torch.complex128)[:2]
+    hs, ps, fs = [], [], []
+    for s, nb, psi, f in mem:
+        h = dftu.handle_for_system(s, nb)
+        h.coulomb_integrals(0)
+        hs.append(h)
+        ps.append(psi.to(dev).clone())
+        fs.append(f)
+    batch = dftu.Batch(hs)
+    with pytest.raises(dftu.DftuError) as e:
+        batch.apply()
+    assert e.value.status == dftu.DFTU_ERR_NOT_READY
+    batch.bind(ps, fs)
+    hs[1].set_vector_potential(torch.tensor([0.1, 0.0, 0.0], dtype=torch.float64, device=dev))
+    with pytest.raises(dftu.DftuError) as e:
+        batch.project()
+    assert e.value.status == dftu.DFTU_ERR_INVALID_ARG
+    hs[1].set_vector_potential(None)
+    hs[1].set_f64_mode(dftu.F64_NATIVE)
+    with pytest.raises(dftu.DftuError) as e:
+        batch.project()
+    assert e.value.status == dftu.DFTU_ERR_INVALID_ARG
+    hs[1].set_f64_mode(dftu.F64_PAIR)
+    batch.project(); batch.occupations(); batch.acbn0_uj(); batch.apply()
+    torch.cuda.synchronize()
+    batch.close()
+    for h in hs:
+        h.close()
