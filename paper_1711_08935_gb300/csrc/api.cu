@@ -25,6 +25,7 @@ dftu_status fail(Ctx* c, dftu_status s, const std::string& msg) {
 }
 
 dftu_status cuda_fail(Ctx* c, cudaError_t e, const char* where) {
+    cudaGetLastError();   // a failed allocation or launch must not leak into the caller's next CUDA check
     return fail(c, e == cudaErrorMemoryAllocation ? DFTU_ERR_ALLOC : DFTU_ERR_CUDA,
                 std::string(where) + ": " + cudaGetErrorString(e));
 }
@@ -149,6 +150,7 @@ dftu_status dftu_create(dftu_handle* out, const dftu_grid* grid, int nk, const d
 
 dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, int nspecies, const dftu_radial* radials,
                              int* npts_out) {
+    NvtxRange nvtx_range("dftu_setup_atoms");
     Ctx* c = reinterpret_cast<Ctx*>(h);
     if (!c) return DFTU_ERR_INVALID_ARG;
     if (c->atoms_ready) return fail(c, DFTU_ERR_INVALID_ARG, "setup_atoms: already called on this handle");
@@ -507,6 +509,7 @@ dftu_status dftu_get_sphere(dftu_handle h, int atom, int32_t* idx_out, int32_t* 
 }
 
 dftu_status dftu_coulomb_integrals(dftu_handle h, int species, double* V_out) {
+    NvtxRange nvtx_range("dftu_coulomb_integrals");
     Ctx* c = reinterpret_cast<Ctx*>(h);
     if (!c) return DFTU_ERR_INVALID_ARG;
     if (!c->atoms_ready) return fail(c, DFTU_ERR_NOT_READY, "coulomb_integrals: call dftu_setup_atoms first");
@@ -581,6 +584,7 @@ dftu_status dftu_set_kernel_variant(dftu_handle h, int which, int variant) {
 int dftu_kernel_variants(int which) { return (which >= 0 && which <= 3) ? NVARIANTS : 0; }
 
 dftu_status dftu_project(dftu_handle h, const void* psi, dftu_prec prec, int nbands, int64_t ld_band, dftu_stream stream) {
+    NvtxRange nvtx_range("dftu_project");
     Ctx* c = reinterpret_cast<Ctx*>(h);
     if (!c) return DFTU_ERR_INVALID_ARG;
     if (!c->atoms_ready) return fail(c, DFTU_ERR_NOT_READY, "project: call dftu_setup_atoms first");
@@ -601,6 +605,7 @@ dftu_status dftu_project(dftu_handle h, const void* psi, dftu_prec prec, int nba
 }
 
 dftu_status dftu_occupations(dftu_handle h, const double* f, dftu_stream stream) {
+    NvtxRange nvtx_range("dftu_occupations");
     Ctx* c = reinterpret_cast<Ctx*>(h);
     if (!c) return DFTU_ERR_INVALID_ARG;
     if (!c->proj_ready) return fail(c, DFTU_ERR_NOT_READY, "occupations: call dftu_project first");
@@ -616,6 +621,7 @@ dftu_status dftu_occupations(dftu_handle h, const double* f, dftu_stream stream)
 }
 
 dftu_status dftu_acbn0_uj(dftu_handle h, dftu_stream stream) {
+    NvtxRange nvtx_range("dftu_acbn0_uj");
     Ctx* c = reinterpret_cast<Ctx*>(h);
     if (!c) return DFTU_ERR_INVALID_ARG;
     if (!c->occ_ready) return fail(c, DFTU_ERR_NOT_READY, "acbn0_uj: call dftu_occupations first");
@@ -635,6 +641,7 @@ dftu_status dftu_acbn0_uj(dftu_handle h, dftu_stream stream) {
 
 dftu_status dftu_apply(dftu_handle h, void* psi_out, dftu_prec prec, int nbands, int64_t ld_band, const double* coef,
                        int accumulate, dftu_stream stream) {
+    NvtxRange nvtx_range("dftu_apply");
     Ctx* c = reinterpret_cast<Ctx*>(h);
     if (!c) return DFTU_ERR_INVALID_ARG;
     if (!c->pot_ready || !c->proj_ready) return fail(c, DFTU_ERR_NOT_READY, "apply: call dftu_project and dftu_acbn0_uj first");
@@ -655,6 +662,7 @@ dftu_status dftu_apply(dftu_handle h, void* psi_out, dftu_prec prec, int nbands,
 
 dftu_status dftu_taylor_step(dftu_handle h, void* psi, void* work, dftu_prec prec, int nbands, int64_t ld_band,
                              const double* f, double dt, int order, dftu_stream stream) {
+    NvtxRange nvtx_range("dftu_taylor_step");
     Ctx* c = reinterpret_cast<Ctx*>(h);
     if (!c) return DFTU_ERR_INVALID_ARG;
     if (!c->atoms_ready) return fail(c, DFTU_ERR_NOT_READY, "taylor_step: call dftu_setup_atoms first");
@@ -693,6 +701,7 @@ dftu_status dftu_taylor_step(dftu_handle h, void* psi, void* work, dftu_prec pre
 
 dftu_status dftu_forces(dftu_handle h, const void* const* dpsi, dftu_prec prec, int nbands, int64_t ld_band, const double* f,
                         double* F_out, dftu_stream stream) {
+    NvtxRange nvtx_range("dftu_forces");
     Ctx* c = reinterpret_cast<Ctx*>(h);
     if (!c) return DFTU_ERR_INVALID_ARG;
     if (!c->pot_ready || !c->proj_ready) return fail(c, DFTU_ERR_NOT_READY, "forces: call dftu_project, dftu_occupations and dftu_acbn0_uj first");
@@ -722,6 +731,7 @@ dftu_status dftu_forces(dftu_handle h, const void* const* dpsi, dftu_prec prec, 
 }
 
 dftu_status dftu_set_vector_potential(dftu_handle h, const double* A, dftu_stream stream) {
+    NvtxRange nvtx_range("dftu_set_vector_potential");
     Ctx* c = reinterpret_cast<Ctx*>(h);
     if (!c) return DFTU_ERR_INVALID_ARG;
     if (!c->atoms_ready) return fail(c, DFTU_ERR_NOT_READY, "set_vector_potential: call dftu_setup_atoms first");
@@ -743,6 +753,7 @@ dftu_status dftu_set_vector_potential(dftu_handle h, const double* A, dftu_strea
 
 dftu_status dftu_hubbard_current(dftu_handle h, const void* psi, dftu_prec prec, int nbands, int64_t ld_band, const double* f,
                                  double* J_out, double* J_atom_out, dftu_stream stream) {
+    NvtxRange nvtx_range("dftu_hubbard_current");
     Ctx* c = reinterpret_cast<Ctx*>(h);
     if (!c) return DFTU_ERR_INVALID_ARG;
     if (!c->pot_ready || !c->proj_ready)
@@ -780,6 +791,7 @@ dftu_status dftu_hubbard_current(dftu_handle h, const void* psi, dftu_prec prec,
 }
 
 dftu_status dftu_fll_energy(dftu_handle h, double* Eee_out, double* Edc_out, dftu_stream stream) {
+    NvtxRange nvtx_range("dftu_fll_energy");
     Ctx* c = reinterpret_cast<Ctx*>(h);
     if (!c) return DFTU_ERR_INVALID_ARG;
     if (!c->pot_ready) return fail(c, DFTU_ERR_NOT_READY, "fll_energy: call dftu_occupations and dftu_acbn0_uj first");
@@ -802,6 +814,7 @@ dftu_status dftu_fll_energy(dftu_handle h, double* Eee_out, double* Edc_out, dft
 
 dftu_status dftu_get_results(dftu_handle h, double* n_out, double* U, double* J, double* EU_atom, double* EU_total,
                              dftu_stream stream) {
+    NvtxRange nvtx_range("dftu_get_results");
     Ctx* c = reinterpret_cast<Ctx*>(h);
     if (!c) return DFTU_ERR_INVALID_ARG;
     if ((n_out && !c->occ_ready) || ((U || J || EU_atom || EU_total) && !c->pot_ready))

@@ -178,6 +178,7 @@ static dftu_status members_uniform(dftu_batch b, const char* what) {
 }
 
 dftu_status dftu_batch_project(dftu_batch b, dftu_stream stream) {
+    dftu::NvtxRange nvtx_range("dftu_batch_project");
     if (!b) return DFTU_ERR_INVALID_ARG;
     if (!b->bound) return bfail(b, DFTU_ERR_NOT_READY, "batch_project: call dftu_batch_bind first");
     if (dftu_status u = members_uniform(b, "batch_project")) return u;
@@ -199,6 +200,7 @@ dftu_status dftu_batch_project(dftu_batch b, dftu_stream stream) {
 }
 
 dftu_status dftu_batch_occupations(dftu_batch b, dftu_stream stream) {
+    dftu::NvtxRange nvtx_range("dftu_batch_occupations");
     if (!b) return DFTU_ERR_INVALID_ARG;
     for (auto* c : b->members)
         if (!c->proj_ready) return bfail(b, DFTU_ERR_NOT_READY, "batch_occupations: call dftu_batch_project first");
@@ -213,6 +215,7 @@ dftu_status dftu_batch_occupations(dftu_batch b, dftu_stream stream) {
 }
 
 dftu_status dftu_batch_acbn0_uj(dftu_batch b, dftu_stream stream) {
+    dftu::NvtxRange nvtx_range("dftu_batch_acbn0_uj");
     if (!b) return DFTU_ERR_INVALID_ARG;
     for (auto* c : b->members) {
         if (!c->occ_ready) return bfail(b, DFTU_ERR_NOT_READY, "batch_acbn0_uj: call dftu_batch_occupations first");
@@ -231,6 +234,7 @@ dftu_status dftu_batch_acbn0_uj(dftu_batch b, dftu_stream stream) {
 }
 
 dftu_status dftu_batch_apply(dftu_batch b, const double* coef, int accumulate, dftu_stream stream) {
+    dftu::NvtxRange nvtx_range("dftu_batch_apply");
     if (!b) return DFTU_ERR_INVALID_ARG;
     if (!b->bound) return bfail(b, DFTU_ERR_NOT_READY, "batch_apply: call dftu_batch_bind first");
     if (dftu_status u = members_uniform(b, "batch_apply")) return u;

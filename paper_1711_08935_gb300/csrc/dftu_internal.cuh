@@ -8,7 +8,18 @@
 
 #include "dftu.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace dftu {
+
+// Names an entry point on profiler timelines (NVTX range for the lifetime of the object; a no-op when no
+// profiler is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr int TILE = 512;      // sphere points per tile (one CTA stages a tile in shared memory)
 constexpr int TILE_PAD = TILE + 128;   // staged orbital rows incl. zero padding read by chained loops (Q*CH <= 128)

@@ -241,6 +241,25 @@ def test_argument_and_order_errors():
     assert e.value.status == dftu.DFTU_ERR_INVALID_ARG
 
 
+def test_allocation_failure_is_reported_and_harmless():
+    """A handle sized for 2^30 bands asks for 550 GB in its first band-sized buffer, more than the device
+    holds: the set-up returns DFTU_ERR_ALLOC (a failed allocation, nothing launched), and the next
+    handle on the same device works normally."""
+    s = C.periodic_two_atoms()
+    with pytest.raises(dftu.DftuError) as e:
+        dftu.handle_for_system(s, 1 << 30)
+    assert e.value.status == dftu.DFTU_ERR_ALLOC
+    nb = 4
+    psi = C.states_np(s, nb, seed=3)
+    f = np.full((s.nk, 2, nb), 0.5)
+    st = O.setup_atoms(s)
+    fixed = [(0.3, 0.02), (0.25, 0.01)]
+    ref = O.hubbard_pass(s, st, psi, f, fixed_u=fixed)
+    out = run_pass(s, psi, f, fixed_u=fixed)
+    assert rel(out["psi_out"], ref["psi_out"]) < 1e-12
+    assert out["status"] == dftu.DFTU_OK
+
+
 NBV = 150
 
 
