@@ -630,18 +630,18 @@ cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_
             case 2: e = run_project<P_F32, 16, 8, 4, 0>(v, a, st); break;
             case 3: e = run_project<P_F32, 4, 16, 4, 0>(v, a, st); break;
             case 4: e = run_project<P_F32, 8, 16, 4, 1>(v, a, st); break;
-            case 5: e = run_project<P_F32, 4, 16, 4, 1>(v, a, st); break;
+            case 5: e = run_project<P_F32, 8, 16, 8, 0>(v, a, st); break;
             case 6: e = run_project<P_F32, 8, 8, 4, 0, 3>(v, a, st); break;
-            case 7: e = run_project<P_F32, 4, 8, 4, 1, 4>(v, a, st); break;
+            case 7: e = run_project<P_F32, 8, 16, 2, 0>(v, a, st); break;
             default: e = run_project<P_F32, 8, 16, 4, 0>(v, a, st); break;
         }
     } else if (mode == DFTU_F64_NATIVE) {
         e = run_project<P_F64, 8, 1, 4, 0>(v, a, st);
     } else {
         switch (variant) {
-            case 1: e = run_project<P_PAIR, 8, 4, 4, 0>(v, a, st); break;
+            case 1: e = run_project<P_PAIR, 4, 8, 8, 1>(v, a, st); break;
             case 2: e = run_project<P_PAIR, 4, 8, 4, 0>(v, a, st); break;
-            case 3: e = run_project<P_PAIR, 8, 8, 1, 0>(v, a, st); break;
+            case 3: e = run_project<P_PAIR, 4, 8, 2, 1>(v, a, st); break;
             case 4: e = run_project<P_PAIR, 4, 8, 4, 1>(v, a, st); break;
             case 5: e = run_project<P_PAIR, 8, 8, 4, 1>(v, a, st); break;
             case 6: e = run_project<P_PAIR, 4, 4, 4, 0, 3>(v, a, st); break;
@@ -704,18 +704,18 @@ cudaError_t launch_project_batch(const BatchLaunch& b, dftu_prec prec, dftu_f64_
             case 2: e = run_project_batch<P_F32, 16, 8, 4, 0>(b, st); break;
             case 3: e = run_project_batch<P_F32, 4, 16, 4, 0>(b, st); break;
             case 4: e = run_project_batch<P_F32, 8, 16, 4, 1>(b, st); break;
-            case 5: e = run_project_batch<P_F32, 4, 16, 4, 1>(b, st); break;
+            case 5: e = run_project_batch<P_F32, 8, 16, 8, 0>(b, st); break;
             case 6: e = run_project_batch<P_F32, 8, 8, 4, 0, 3>(b, st); break;
-            case 7: e = run_project_batch<P_F32, 4, 8, 4, 1, 4>(b, st); break;
+            case 7: e = run_project_batch<P_F32, 8, 16, 2, 0>(b, st); break;
             default: e = run_project_batch<P_F32, 8, 16, 4, 0>(b, st); break;
         }
     } else if (mode == DFTU_F64_NATIVE) {
         e = run_project_batch<P_F64, 8, 1, 4, 0>(b, st);
     } else {
         switch (variant) {
-            case 1: e = run_project_batch<P_PAIR, 8, 4, 4, 0>(b, st); break;
+            case 1: e = run_project_batch<P_PAIR, 4, 8, 8, 1>(b, st); break;
             case 2: e = run_project_batch<P_PAIR, 4, 8, 4, 0>(b, st); break;
-            case 3: e = run_project_batch<P_PAIR, 8, 8, 1, 0>(b, st); break;
+            case 3: e = run_project_batch<P_PAIR, 4, 8, 2, 1>(b, st); break;
             case 4: e = run_project_batch<P_PAIR, 4, 8, 4, 1>(b, st); break;
             case 5: e = run_project_batch<P_PAIR, 8, 8, 4, 1>(b, st); break;
             case 6: e = run_project_batch<P_PAIR, 4, 4, 4, 0, 3>(b, st); break;
