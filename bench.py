@@ -35,8 +35,8 @@ WORKLOAD = "oxide supercell 96^3 h=0.25, 8 TM(3d,R4.5)+8 O(2p,R3.5), 256 bands, 
 # DRAM bytes per state (one band of one k-point and spin) measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum) on the 64-band oxide case for the kernel variants named here; see
 # profiles/pair_project_apply_oxide_small.md.  Valid only while that variant is the one timed.
-NCU_TRAFFIC_PER_STATE = {("project", 4): (808.505088e6 + 13.654528e6) / 128,
-                         ("apply", 4): (806.807552e6 + 573.596672e6) / 128}
+NCU_TRAFFIC_PER_STATE = {("project", 1): (808.521472e6 + 13.469184e6) / 128,
+                         ("apply", 4): (806.894080e6 + 573.875200e6) / 128}
 
 
 def measured_peaks():
