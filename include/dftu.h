@@ -32,7 +32,9 @@
  *   - Spin-unpolarised runs hold one channel whose occupations are per spin; spin sums count it twice.
  *   - Every compute call is asynchronous on the given stream (a cudaStream_t passed as void*;
  *     NULL = legacy default stream) and allocates nothing: all device memory is allocated by
- *     dftu_create and dftu_setup_atoms.  Errors detected on the device (non-finite projections,
+ *     dftu_create and dftu_setup_atoms.  The calls of one handle share its buffers (projections,
+ *     tile partials, occupation counters), so they must be ordered: one stream, or streams the
+ *     caller orders with events.  Different handles are independent.  Errors detected on the device (non-finite projections,
  *     zero ACBN0 denominators) set bits of a device status word read by dftu_sync_status.
  *   - Return value: DFTU_OK, or an error code; dftu_last_error() gives a message.  On an argument
  *     error nothing is launched and the handle is unchanged.
