@@ -190,7 +190,8 @@ dftu_status dftu_taylor_step(dftu_handle h, void* psi, void* work, dftu_prec pre
  * while dftu_occupations and dftu_acbn0_uj are unchanged (they read p^A).  A: device pointer to three
  * FP64 numbers (atomic units, the phase is A.d with d in bohr), read by a kernel on `stream` when it
  * runs, so a graph may capture this call and replay it after A changes.  A = NULL switches the phases
- * off.  Either way the handle's projections, occupations and potential are marked stale.
+ * off.  Setting A, or clearing one that was set, marks the handle's projections, occupations and
+ * potential stale (the next dftu_apply then needs a new dftu_project / occupations / acbn0).
  * Collinear and unpolarised states only (INVALID_ARG for a non-collinear handle with A != NULL);
  * dftu_forces returns INVALID_ARG while A is set.  Launches only, no synchronisation. */
 dftu_status dftu_set_vector_potential(dftu_handle h, const double* A, dftu_stream stream);

@@ -738,6 +738,7 @@ dftu_status dftu_set_vector_potential(dftu_handle h, const double* A, dftu_strea
     if (c->spin == DFTU_NONCOLLINEAR && A)
         return fail(c, DFTU_ERR_INVALID_ARG, "set_vector_potential: the gauge-invariant operator is built for collinear and unpolarised states");
     if (!A) {
+        if (c->gauge_on) c->proj_ready = c->occ_ready = c->pot_ready = false;   // made with the phases
         c->gauge_on = false;
         return DFTU_OK;
     }

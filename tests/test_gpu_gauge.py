@@ -232,6 +232,11 @@ def test_gauge_argument_errors():
     with pytest.raises(dftu.DftuError) as e:
         h.hubbard_current(t, fd)
     assert e.value.status == dftu.DFTU_ERR_NOT_READY
+    h.project(t); h.occupations(fd); h.acbn0_uj()
+    h.set_vector_potential(None)                             # clearing A makes them stale too
+    with pytest.raises(dftu.DftuError) as e:
+        h.apply(t)
+    assert e.value.status == dftu.DFTU_ERR_NOT_READY
     with pytest.raises(ValueError):
         h.set_vector_potential(torch.zeros(3, dtype=torch.float32, device=dev))
     h.close()
