@@ -427,6 +427,14 @@ static cudaError_t run_apply(const View& v, ApplyArgs a, const int* color_order,
     return cudaSuccess;
 }
 
+// The shapes selectable with dftu_set_kernel_variant, listed once for the single-system and the batched
+// launches: X(variant, lanes per band Q, band groups per CTA, points in flight per lane, L2 prefetch).
+// Variant 0, and 6 and 7, take the default case of each switch.
+#define DFTU_APPLY_SHAPES_F32(X) X(1, 8, 4, 4, 0) X(2, 4, 4, 8, 0) X(3, 16, 4, 4, 0) X(4, 8, 4, 8, 1) X(5, 8, 4, 4, 1)
+#define DFTU_APPLY_DEFAULT_F32 8, 4, 8, 0
+#define DFTU_APPLY_SHAPES_PAIR(X) X(1, 8, 4, 2, 0) X(2, 4, 4, 4, 0) X(3, 8, 4, 8, 0) X(4, 8, 4, 4, 1) X(5, 4, 4, 4, 1)
+#define DFTU_APPLY_DEFAULT_PAIR 8, 4, 4, 0
+
 cudaError_t launch_apply(const View& v, void* psi, dftu_prec prec, dftu_f64_mode mode, int nbands,
                          int64_t sk, int64_t ss, int64_t sn, const double* coef, const int* color_order,
                          const std::vector<int>& color_beg, int variant, int accumulate, cudaStream_t st, bool gauge) {
@@ -436,25 +444,21 @@ cudaError_t launch_apply(const View& v, void* psi, dftu_prec prec, dftu_f64_mode
         if (mode == DFTU_F64_NATIVE) return run_apply<A_F64, 8, 4, 4, 0, 1>(v, a, color_order, color_beg, st);
         return run_apply<A_PAIR, 8, 4, 4, 1, 1>(v, a, color_order, color_beg, st);
     }
+#define DFTU_CASE_F32(i, Q, NBG, U, PF) case i: return run_apply<A_F32, Q, NBG, U, PF>(v, a, color_order, color_beg, st);
+#define DFTU_CASE_PAIR(i, Q, NBG, U, PF) case i: return run_apply<A_PAIR, Q, NBG, U, PF>(v, a, color_order, color_beg, st);
     if (prec == DFTU_C64) {
-        switch (variant) {   // (lanes per band, band groups per CTA, points in flight per lane)
-            case 1: return run_apply<A_F32, 8, 4, 4, 0>(v, a, color_order, color_beg, st);
-            case 2: return run_apply<A_F32, 4, 4, 8, 0>(v, a, color_order, color_beg, st);
-            case 3: return run_apply<A_F32, 16, 4, 4, 0>(v, a, color_order, color_beg, st);
-            case 4: return run_apply<A_F32, 8, 4, 8, 1>(v, a, color_order, color_beg, st);
-            case 5: return run_apply<A_F32, 8, 4, 4, 1>(v, a, color_order, color_beg, st);
-            default: return run_apply<A_F32, 8, 4, 8, 0>(v, a, color_order, color_beg, st);
+        switch (variant) {
+            DFTU_APPLY_SHAPES_F32(DFTU_CASE_F32)
+            default: return run_apply<A_F32, DFTU_APPLY_DEFAULT_F32>(v, a, color_order, color_beg, st);
         }
     }
     if (mode == DFTU_F64_NATIVE) return run_apply<A_F64, 8, 4, 4, 0>(v, a, color_order, color_beg, st);
     switch (variant) {
-        case 1: return run_apply<A_PAIR, 8, 4, 2, 0>(v, a, color_order, color_beg, st);
-        case 2: return run_apply<A_PAIR, 4, 4, 4, 0>(v, a, color_order, color_beg, st);
-        case 3: return run_apply<A_PAIR, 8, 4, 8, 0>(v, a, color_order, color_beg, st);
-        case 4: return run_apply<A_PAIR, 8, 4, 4, 1>(v, a, color_order, color_beg, st);
-        case 5: return run_apply<A_PAIR, 4, 4, 4, 1>(v, a, color_order, color_beg, st);
-        default: return run_apply<A_PAIR, 8, 4, 4, 0>(v, a, color_order, color_beg, st);
+        DFTU_APPLY_SHAPES_PAIR(DFTU_CASE_PAIR)
+        default: return run_apply<A_PAIR, DFTU_APPLY_DEFAULT_PAIR>(v, a, color_order, color_beg, st);
     }
+#undef DFTU_CASE_F32
+#undef DFTU_CASE_PAIR
 }
 
 // Taylor coefficients of exp(-i dt H): term j = (-i dt / j) H term_{j-1}.
@@ -496,25 +500,21 @@ static cudaError_t run_apply_batch(const BatchLaunch& b, const double* coef, int
 
 cudaError_t launch_apply_batch(const BatchLaunch& b, dftu_prec prec, dftu_f64_mode mode, int variant, const double* coef,
                                int accumulate, cudaStream_t st) {
+#define DFTU_CASE_F32(i, Q, NBG, U, PF) case i: return run_apply_batch<A_F32, Q, NBG, U, PF>(b, coef, accumulate, st);
+#define DFTU_CASE_PAIR(i, Q, NBG, U, PF) case i: return run_apply_batch<A_PAIR, Q, NBG, U, PF>(b, coef, accumulate, st);
     if (prec == DFTU_C64) {
         switch (variant) {
-            case 1: return run_apply_batch<A_F32, 8, 4, 4, 0>(b, coef, accumulate, st);
-            case 2: return run_apply_batch<A_F32, 4, 4, 8, 0>(b, coef, accumulate, st);
-            case 3: return run_apply_batch<A_F32, 16, 4, 4, 0>(b, coef, accumulate, st);
-            case 4: return run_apply_batch<A_F32, 8, 4, 8, 1>(b, coef, accumulate, st);
-            case 5: return run_apply_batch<A_F32, 8, 4, 4, 1>(b, coef, accumulate, st);
-            default: return run_apply_batch<A_F32, 8, 4, 8, 0>(b, coef, accumulate, st);
+            DFTU_APPLY_SHAPES_F32(DFTU_CASE_F32)
+            default: return run_apply_batch<A_F32, DFTU_APPLY_DEFAULT_F32>(b, coef, accumulate, st);
         }
     }
     if (mode == DFTU_F64_NATIVE) return run_apply_batch<A_F64, 8, 4, 4, 0>(b, coef, accumulate, st);
     switch (variant) {
-        case 1: return run_apply_batch<A_PAIR, 8, 4, 2, 0>(b, coef, accumulate, st);
-        case 2: return run_apply_batch<A_PAIR, 4, 4, 4, 0>(b, coef, accumulate, st);
-        case 3: return run_apply_batch<A_PAIR, 8, 4, 8, 0>(b, coef, accumulate, st);
-        case 4: return run_apply_batch<A_PAIR, 8, 4, 4, 1>(b, coef, accumulate, st);
-        case 5: return run_apply_batch<A_PAIR, 4, 4, 4, 1>(b, coef, accumulate, st);
-        default: return run_apply_batch<A_PAIR, 8, 4, 4, 0>(b, coef, accumulate, st);
+        DFTU_APPLY_SHAPES_PAIR(DFTU_CASE_PAIR)
+        default: return run_apply_batch<A_PAIR, DFTU_APPLY_DEFAULT_PAIR>(b, coef, accumulate, st);
     }
+#undef DFTU_CASE_F32
+#undef DFTU_CASE_PAIR
 }
 
 }  // namespace dftu

@@ -616,39 +616,43 @@ static cudaError_t run_project(const View& v, const ProjArgs& a, cudaStream_t st
     return cudaGetLastError();
 }
 
+// The shapes selectable with dftu_set_kernel_variant, listed once for the single-system and the batched
+// launches: X(variant, lanes per band Q, points per chain, band groups per CTA, L2 prefetch, minimum
+// blocks per SM).  Variant 0 is the default case of each switch.
+#define DFTU_PROJECT_SHAPES_F32(X) \
+    X(1, 8, 8, 4, 0, 2) X(2, 16, 8, 4, 0, 2) X(3, 4, 16, 4, 0, 2) X(4, 8, 16, 4, 1, 2) \
+    X(5, 8, 16, 8, 0, 2) X(6, 8, 8, 4, 0, 3) X(7, 8, 16, 2, 0, 2)
+#define DFTU_PROJECT_DEFAULT_F32 8, 16, 4, 0, 2
+#define DFTU_PROJECT_SHAPES_PAIR(X) \
+    X(1, 4, 8, 8, 1, 2) X(2, 4, 8, 4, 0, 2) X(3, 4, 8, 2, 1, 2) X(4, 4, 8, 4, 1, 2) \
+    X(5, 8, 8, 4, 1, 2) X(6, 4, 4, 4, 0, 3) X(7, 4, 8, 4, 1, 3)
+#define DFTU_PROJECT_DEFAULT_PAIR 8, 8, 4, 0, 2
+
 cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_f64_mode mode, int nbands,
                            int64_t sk, int64_t ss, int64_t sn, int variant, cudaStream_t st, bool gauge) {
     ProjArgs a{psi, sk, ss, sn, nbands};
     cudaError_t e;
+#define DFTU_CASE_F32(i, Q, CH, NBG, PF, MB) case i: e = run_project<P_F32, Q, CH, NBG, PF, MB>(v, a, st); break;
+#define DFTU_CASE_PAIR(i, Q, CH, NBG, PF, MB) case i: e = run_project<P_PAIR, Q, CH, NBG, PF, MB>(v, a, st); break;
     if (gauge) {   // one shape per arithmetic policy with the gauge phases (Sec. V)
         if (prec == DFTU_C64) e = run_project<P_F32, 8, 16, 4, 0, 2, 1>(v, a, st);
         else if (mode == DFTU_F64_NATIVE) e = run_project<P_F64, 8, 1, 4, 0, 2, 1>(v, a, st);
         else e = run_project<P_PAIR, 4, 8, 4, 1, 2, 1>(v, a, st);
     } else if (prec == DFTU_C64) {
-        switch (variant) {   // (lanes per band, points per chain, band groups per CTA)
-            case 1: e = run_project<P_F32, 8, 8, 4, 0>(v, a, st); break;
-            case 2: e = run_project<P_F32, 16, 8, 4, 0>(v, a, st); break;
-            case 3: e = run_project<P_F32, 4, 16, 4, 0>(v, a, st); break;
-            case 4: e = run_project<P_F32, 8, 16, 4, 1>(v, a, st); break;
-            case 5: e = run_project<P_F32, 8, 16, 8, 0>(v, a, st); break;
-            case 6: e = run_project<P_F32, 8, 8, 4, 0, 3>(v, a, st); break;
-            case 7: e = run_project<P_F32, 8, 16, 2, 0>(v, a, st); break;
-            default: e = run_project<P_F32, 8, 16, 4, 0>(v, a, st); break;
+        switch (variant) {
+            DFTU_PROJECT_SHAPES_F32(DFTU_CASE_F32)
+            default: e = run_project<P_F32, DFTU_PROJECT_DEFAULT_F32>(v, a, st); break;
         }
     } else if (mode == DFTU_F64_NATIVE) {
         e = run_project<P_F64, 8, 1, 4, 0>(v, a, st);
     } else {
         switch (variant) {
-            case 1: e = run_project<P_PAIR, 4, 8, 8, 1>(v, a, st); break;
-            case 2: e = run_project<P_PAIR, 4, 8, 4, 0>(v, a, st); break;
-            case 3: e = run_project<P_PAIR, 4, 8, 2, 1>(v, a, st); break;
-            case 4: e = run_project<P_PAIR, 4, 8, 4, 1>(v, a, st); break;
-            case 5: e = run_project<P_PAIR, 8, 8, 4, 1>(v, a, st); break;
-            case 6: e = run_project<P_PAIR, 4, 4, 4, 0, 3>(v, a, st); break;
-            case 7: e = run_project<P_PAIR, 4, 8, 4, 1, 3>(v, a, st); break;
-            default: e = run_project<P_PAIR, 8, 8, 4, 0>(v, a, st); break;
+            DFTU_PROJECT_SHAPES_PAIR(DFTU_CASE_PAIR)
+            default: e = run_project<P_PAIR, DFTU_PROJECT_DEFAULT_PAIR>(v, a, st); break;
         }
     }
+#undef DFTU_CASE_F32
+#undef DFTU_CASE_PAIR
     if (e != cudaSuccess) return e;
     int64_t n = (int64_t)v.nk * v.ns * nbands * v.MT;
     k_tile_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(v, nbands);
@@ -698,31 +702,23 @@ static cudaError_t run_project_batch(const BatchLaunch& b, cudaStream_t st) {
 
 cudaError_t launch_project_batch(const BatchLaunch& b, dftu_prec prec, dftu_f64_mode mode, int variant, cudaStream_t st) {
     cudaError_t e;
+#define DFTU_CASE_F32(i, Q, CH, NBG, PF, MB) case i: e = run_project_batch<P_F32, Q, CH, NBG, PF, MB>(b, st); break;
+#define DFTU_CASE_PAIR(i, Q, CH, NBG, PF, MB) case i: e = run_project_batch<P_PAIR, Q, CH, NBG, PF, MB>(b, st); break;
     if (prec == DFTU_C64) {
         switch (variant) {
-            case 1: e = run_project_batch<P_F32, 8, 8, 4, 0>(b, st); break;
-            case 2: e = run_project_batch<P_F32, 16, 8, 4, 0>(b, st); break;
-            case 3: e = run_project_batch<P_F32, 4, 16, 4, 0>(b, st); break;
-            case 4: e = run_project_batch<P_F32, 8, 16, 4, 1>(b, st); break;
-            case 5: e = run_project_batch<P_F32, 8, 16, 8, 0>(b, st); break;
-            case 6: e = run_project_batch<P_F32, 8, 8, 4, 0, 3>(b, st); break;
-            case 7: e = run_project_batch<P_F32, 8, 16, 2, 0>(b, st); break;
-            default: e = run_project_batch<P_F32, 8, 16, 4, 0>(b, st); break;
+            DFTU_PROJECT_SHAPES_F32(DFTU_CASE_F32)
+            default: e = run_project_batch<P_F32, DFTU_PROJECT_DEFAULT_F32>(b, st); break;
         }
     } else if (mode == DFTU_F64_NATIVE) {
         e = run_project_batch<P_F64, 8, 1, 4, 0>(b, st);
     } else {
         switch (variant) {
-            case 1: e = run_project_batch<P_PAIR, 4, 8, 8, 1>(b, st); break;
-            case 2: e = run_project_batch<P_PAIR, 4, 8, 4, 0>(b, st); break;
-            case 3: e = run_project_batch<P_PAIR, 4, 8, 2, 1>(b, st); break;
-            case 4: e = run_project_batch<P_PAIR, 4, 8, 4, 1>(b, st); break;
-            case 5: e = run_project_batch<P_PAIR, 8, 8, 4, 1>(b, st); break;
-            case 6: e = run_project_batch<P_PAIR, 4, 4, 4, 0, 3>(b, st); break;
-            case 7: e = run_project_batch<P_PAIR, 4, 8, 4, 1, 3>(b, st); break;
-            default: e = run_project_batch<P_PAIR, 8, 8, 4, 0>(b, st); break;
+            DFTU_PROJECT_SHAPES_PAIR(DFTU_CASE_PAIR)
+            default: e = run_project_batch<P_PAIR, DFTU_PROJECT_DEFAULT_PAIR>(b, st); break;
         }
     }
+#undef DFTU_CASE_F32
+#undef DFTU_CASE_PAIR
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((b.max_reduce + 255) / 256), b.nsys);
     k_tile_reduce_batch<<<grid, 256, 0, st>>>(b.views, b.args);
