@@ -635,7 +635,7 @@ cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_
 #define DFTU_CASE_F32(i, Q, CH, NBG, PF, MB) case i: e = run_project<P_F32, Q, CH, NBG, PF, MB>(v, a, st); break;
 #define DFTU_CASE_PAIR(i, Q, CH, NBG, PF, MB) case i: e = run_project<P_PAIR, Q, CH, NBG, PF, MB>(v, a, st); break;
     if (gauge) {   // one shape per arithmetic policy with the gauge phases (Sec. V)
-        if (prec == DFTU_C64) e = run_project<P_F32, 8, 16, 4, 0, 2, 1>(v, a, st);
+        if (prec == DFTU_C64) e = run_project<P_F32, 8, 16, 8, 0, 2, 1>(v, a, st);
         else if (mode == DFTU_F64_NATIVE) e = run_project<P_F64, 8, 1, 4, 0, 2, 1>(v, a, st);
         else e = run_project<P_PAIR, 4, 8, 4, 1, 2, 1>(v, a, st);
     } else if (prec == DFTU_C64) {
@@ -665,7 +665,7 @@ cudaError_t launch_project_dirs(const View& v, const void* psi, dftu_prec prec, 
     ProjArgs a{psi, sk, ss, sn, nbands};
     cudaError_t e;
     // the fixed shapes of the gauge path, with and without the phases
-    if (prec == DFTU_C64) e = gauge ? run_project<P_F32, 8, 16, 4, 0, 2, 1, 3>(v, a, st) : run_project<P_F32, 8, 16, 4, 0, 2, 0, 3>(v, a, st);
+    if (prec == DFTU_C64) e = gauge ? run_project<P_F32, 8, 16, 8, 0, 2, 1, 3>(v, a, st) : run_project<P_F32, 8, 16, 8, 0, 2, 0, 3>(v, a, st);
     else if (mode == DFTU_F64_NATIVE) e = gauge ? run_project<P_F64, 8, 1, 4, 0, 2, 1, 3>(v, a, st) : run_project<P_F64, 8, 1, 4, 0, 2, 0, 3>(v, a, st);
     else e = gauge ? run_project<P_PAIR, 4, 8, 4, 1, 2, 1, 3>(v, a, st) : run_project<P_PAIR, 4, 8, 4, 1, 2, 0, 3>(v, a, st);
     if (e != cudaSuccess) return e;
