@@ -9,7 +9,7 @@ by the projection and read + written by the apply (complex128: 16 B per point).
 
 Prints ONE JSON line (rank 0).  --impl reference times the CPU FP64 oracle on a bounded sample of the
 same workload instead.  Under torchrun every rank runs an independent replica (the pass has no
-cross-GPU exchange in this build), timing is the max over ranks.
+cross-GPU exchange), timing is the max over ranks.
 """
 from __future__ import annotations
 
