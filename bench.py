@@ -241,7 +241,14 @@ def run_ours(args):
     # ---- end to end through the public API with host (pinned) states
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, h, s, nb, f, dev, step_bytes64, ws)
+        # every rank pins its own host copy of the states: skip the leg if the copies would not fit
+        host_ram = os.sysconf("SC_PHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+        need = ws * host_bytes(s, nb)
+        if need > 0.75 * host_ram:
+            e2e = {"skipped": f"{ws} ranks x {host_bytes(s, nb) / 1e9:.0f} GB of pinned host states exceed "
+                              f"0.75 of the host's {host_ram / 1e9:.0f} GB"}
+        else:
+            e2e = run_e2e(args, h, s, nb, f, dev, step_bytes64, ws)
 
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
