@@ -44,6 +44,21 @@ def test_sphere_map_canonical_order_and_folding():
     assert len({tuple(t) for t in sm["T"]}) == 8                        # 2R > L: two cells per axis
 
 
+def test_sphere_boundary_is_inclusive():
+    """Points exactly on the sphere belong to it (the inclusive reading of Sec. II).  With h = 0.5,
+    R = 2.5 and the atom on a grid point, every squared distance is exact in binary: the sphere holds
+    the integer points with i^2 + j^2 + k^2 <= 25, 30 of them on the boundary (the permutations and
+    signs of (5, 0, 0) and (3, 4, 0))."""
+    g = synth.Grid((16, 16, 16), (0.5, 0.5, 0.5), periodic=False)
+    sm = O.sphere_map(g, synth.Atom((4.0, 4.0, 4.0), 0, 2, 2.5))
+    r = np.arange(-5, 6)
+    I, J, K = np.meshgrid(r, r, r, indexing="ij")
+    q = I * I + J * J + K * K
+    assert int(np.sum(q == 25)) == 30
+    assert len(sm["idx"]) == int(np.sum(q <= 25)) == 515
+    assert int(np.sum(sm["r"] == 2.5)) == 30
+
+
 def test_radial_interpolation_exact_on_cubics_and_converges():
     dr = 0.05
     r = np.arange(200) * dr
@@ -155,6 +170,50 @@ def test_occupations_hermitian_bounded_and_nbar_bounds():
             assert ev.min() > -1e-13 and ev.max() < 1 + 1e-12
 
 
+def _scaled_orbital_states(s, st, a, b=None):
+    """psi_n = a_n phi_{0,n,k} (the Bloch orbitals of atom 0 on the cell); with b, spinors
+    (a_n phi_{0,n,k}, b_n phi_{0,n,k}).  Returns psi in the system's layout."""
+    M = len(a)
+    out = np.zeros((s.nk, 2, M, s.grid.npts) if b is None else (s.nk, M, 2, s.grid.npts), dtype=np.complex128)
+    for ik in range(s.nk):
+        g = O.bloch_orbitals_on_grid(s, st, s.kpts[ik])[0]
+        if b is None:
+            out[ik, :] = (np.asarray(a)[:, None] * g)[None]
+        else:
+            out[ik, :, 0] = np.asarray(a)[:, None] * g
+            out[ik, :, 1] = np.asarray(b)[:, None] * g
+    return out
+
+
+def test_nbar_closed_form_for_scaled_orbital_states():
+    """Eq. (9): Nbar_{nk} sums |p|^2 over the atoms of one species and over m.  The d atom (species 0)
+    and the p atom (species 1) have disjoint spheres that do not reach their own images, so the
+    states psi_n = a_n phi_{0,n,k} project as p_{0,m,n} = a_n delta_mn and not at all onto the p atom:
+    Nbar^0_n = a_n^2 and Nbar^1_n = 0 at every k and spin."""
+    s = C.periodic_two_atoms()
+    st = O.setup_atoms(s)
+    a = np.array([0.9, 0.3, 0.6, 0.8, 0.45])
+    p = O.project(s, st, _scaled_orbital_states(s, st, a))
+    assert np.allclose(p[0], np.diag(a)[None, None], atol=1e-13)
+    nb = O.nbar(s, p)
+    assert np.allclose(nb[0], (a * a)[None, None], atol=1e-13)
+    assert np.allclose(nb[1], 0.0, atol=1e-13)
+
+
+def test_nbar_closed_form_for_scaled_orbital_spinors():
+    """Eq. (B4): for spinors Nbar also sums over both components, so (a_n phi_n, b_n phi_n) gives
+    Nbar^0_n = a_n^2 + b_n^2 and Nbar^1_n = 0."""
+    s = C.periodic_two_atoms(nspin=1)
+    s.noncollinear = True
+    st = O.setup_atoms(s)
+    a = np.array([0.9, 0.3, 0.6, 0.8, 0.45])
+    b = np.array([0.1, 0.7, 0.5, 0.2, 0.6])
+    p = O.project_nc(s, st, _scaled_orbital_states(s, st, a, b))
+    nb = O.nbar(s, p, noncollinear=True)
+    assert np.allclose(nb[0], (a * a + b * b)[None], atol=1e-13)
+    assert np.allclose(nb[1], 0.0, atol=1e-13)
+
+
 def test_lattice_translation_leaves_occupations_unchanged():
     """Moving an atom by a lattice vector only relabels images: n is unchanged (Sec. II phase)."""
     s = C.periodic_two_atoms()
@@ -251,6 +310,24 @@ def test_taylor_step_matches_exponential_and_conserves_norm():
     n0 = s.grid.dV * np.sum(np.abs(psi) ** 2, axis=-1)
     n1 = s.grid.dV * np.sum(np.abs(out) ** 2, axis=-1)
     assert np.max(np.abs(n1 - n0)) < 1e-12
+
+
+def test_taylor_step_on_eigenstates_is_the_fourth_order_polynomial():
+    """Sec. V step on eigenstates of V_U: with psi_m = phi_m and occupations f_m, n = diag(f) and
+    V = U_eff diag(1/2 - f) (Eq. 6), so V_U psi_m = lambda_m psi_m with lambda_m = U_eff (1/2 - f_m),
+    and one step multiplies psi_m by sum_{j<=4} (-i lambda_m dt)^j / j! exactly.  With |lambda dt|
+    up to 0.3 a propagator of another order or sign misses this by far more than rounding."""
+    s = synth.tiny_system()
+    st = O.setup_atoms(s)
+    psi = O.bloch_orbitals_on_grid(s, st, s.kpts[0])[0][None, None].copy()
+    f = np.array([[[1.0, 0.8, 0.5, 0.2, 0.0]]])
+    U, J, dt = 0.6, 0.1, 1.2
+    out, _ = O.taylor_step(s, st, psi, f, dt, fixed_u=[(U, J)])
+    lam = (U - J) * (0.5 - f[0, 0])
+    for m in range(5):
+        x = -1j * lam[m] * dt
+        T4 = sum(x ** j / math.factorial(j) for j in range(5))
+        assert np.max(np.abs(out[0, 0, m] - T4 * psi[0, 0, m])) < 1e-13 * np.max(np.abs(psi))
 
 
 # --------------------------------------------------------------------------- ACBN0 U, J
