@@ -99,6 +99,10 @@ dftu_status dftu_create(dftu_handle* out, const dftu_grid* grid, int nk, const d
  * m = -l..l: p = y,z,x; d = xy,yz,3z^2-r^2,xz,x^2-y^2) and orthonormalise each atom's orbitals
  * with S^{-1/2}, S = dV phi^T phi (Sec. III assumes an orthogonal basis on each atom).
  * atoms, radials: host arrays (copied).  npts_out: host [natoms] sphere point counts, or NULL.
+ * S^{-1/2} exists only for orbitals that are linearly independent on the sphere: an atom whose
+ * overlap has lambda_min <= 1e-10 lambda_max (fewer useful points than orbitals, or a radial
+ * function that vanishes on the sphere) is refused with DFTU_ERR_INVALID_ARG, as is an atom with
+ * no grid point in its sphere; the handle then has no atoms and should be destroyed.
  * Blocking (synchronises the device).  May be called once per handle. */
 dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, int nspecies,
                              const dftu_radial* radials, int* npts_out);

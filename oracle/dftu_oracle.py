@@ -29,7 +29,9 @@ Readings of points the paper leaves open (each is also recorded in the design no
     fused multiply-add, dx = (i*h + origin) - X, canonical order z-major then y then x over
     unfolded integer coordinates; isolated boxes drop points outside the box.
   * Per-atom Loewdin orthonormalisation of the truncated orbitals (Sec. III assumes an
-    orthogonal basis on each atom).
+    orthogonal basis on each atom).  S^{-1/2} exists only for orbitals that are linearly
+    independent on the sphere: an atom whose overlap has lambda_min <= 1e-10 lambda_max (fewer
+    useful points than orbitals, a radial function that vanishes there) is refused.
   * Ubar/Jbar numerators use Pbar_{mm'} Pbar_{m''m'''} as in Eq. (7) (the printed m'm'' index
     in Eqs. 10-11 is read as a typo); the denominators use N_m = n_mm literally.
   * Spin-unpolarised runs store one channel whose occupations f are per spin; every spin sum
@@ -49,6 +51,7 @@ from typing import Dict, List, Sequence
 import numpy as np
 
 ZERO_DENOM = 1e-14
+LOWDIN_MIN_RATIO = 1e-10
 HARTREE_EV = 27.211386245988
 
 
@@ -166,6 +169,8 @@ def lowdin(phi: np.ndarray, dV: float) -> np.ndarray:
     localised basis on each atom is orthogonal)."""
     S = dV * (phi.T @ phi)
     lam, U = np.linalg.eigh(S)
+    if not (np.all(np.isfinite(lam)) and lam[-1] > 0 and lam[0] > LOWDIN_MIN_RATIO * lam[-1]):
+        raise ValueError("orbitals are linearly dependent on the sphere: S^{-1/2} does not exist")
     return phi @ (U @ np.diag(lam ** -0.5) @ U.T)
 
 

@@ -450,15 +450,25 @@ dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, 
     if (e == cudaSuccess) e = dalloc(c, &v.E, (size_t)natoms);
     if (e == cudaSuccess) e = dalloc(c, &v.Etot, 1);
     double* work = nullptr;
-    if (e == cudaSuccess) e = dalloc(c, &work, (size_t)natoms * MAXM * MAXM);
+    if (e == cudaSuccess) e = dalloc(c, &work, (size_t)natoms * MAXM * MAXM + natoms);   // overlaps, then conditions
     if (e != cudaSuccess) return cuda_fail(c, e, "setup_atoms: work buffers");
     // ---- phases, orbitals, Loewdin ----
     e = launch_seg_phases(v, 0);
     if (e == cudaSuccess) e = launch_orbitals(v, d_rtab, d_roff, d_rnr, d_rdr, 0);
-    if (e == cudaSuccess) e = launch_lowdin(v, work, 0);
+    double* cond = work + (size_t)natoms * MAXM * MAXM;
+    if (e == cudaSuccess) e = launch_lowdin(v, work, cond, 0);
     if (e == cudaSuccess) e = launch_displaced_orbitals(v, phi_off, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(c, e, "setup_atoms: orbitals");
+    // S^(-1/2) exists only for orbitals that are linearly independent on the sphere (Sec. III)
+    std::vector<double> hcond(natoms);
+    e = cudaMemcpy(hcond.data(), cond, sizeof(double) * natoms, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "setup_atoms: overlap conditions");
+    for (int a = 0; a < natoms; ++a)
+        if (!(hcond[a] > LOWDIN_MIN_RATIO))
+            return fail(c, DFTU_ERR_INVALID_ARG, "setup_atoms: the orbitals of atom " + std::to_string(a) +
+                                                 " are linearly dependent on its sphere (overlap eigenvalue ratio " +
+                                                 std::to_string(hcond[a]) + ")");
     if (npts_out)
         for (int a = 0; a < natoms; ++a) npts_out[a] = c->npts[a];
     c->atoms_ready = true;

@@ -30,6 +30,8 @@ constexpr int CTA = 256;       // threads per CTA of the streaming kernels
 constexpr int MAX_TAYLOR = 8;  // highest Taylor order of dftu_taylor_step
 constexpr int OCC_SPLIT = 8;   // CTAs sharing the (k, band) sum of one occupation matrix
 constexpr int OCC_MAXP = (2 * MAXM) * (2 * MAXM);   // largest matrix (non-collinear f shell), elements
+constexpr double LOWDIN_MIN_RATIO = 1e-10;   // smallest accepted lambda_min / lambda_max of an atom's orbital
+                                            // overlap; below it S^(-1/2) is refused (orbitals dependent)
 
 enum StatusBits : int { ST_NONFINITE = 1, ST_ZERO_DENOM = 2, ST_TIMEOUT = 4 };
 
@@ -182,7 +184,7 @@ cudaError_t launch_sphere_flags(const View& v, const double* pos, const double* 
 cudaError_t launch_seg_phases(const View& v, cudaStream_t st);
 cudaError_t launch_orbitals(const View& v, const double* radial_tab, const int* radial_off,
                             const int* radial_nr, const double* radial_dr, cudaStream_t st);
-cudaError_t launch_lowdin(const View& v, double* work_S, cudaStream_t st);
+cudaError_t launch_lowdin(const View& v, double* work_S, double* cond, cudaStream_t st);
 
 constexpr int NVARIANTS = 8;   // shapes per streaming kernel (see dftu_set_kernel_variant)
 cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_f64_mode mode, int nbands,

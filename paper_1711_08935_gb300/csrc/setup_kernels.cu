@@ -165,7 +165,10 @@ __global__ void k_overlap(View v, double* __restrict__ S) {
 
 // Cyclic Jacobi diagonalisation of the symmetric S (one thread per atom), then T = S^{-1/2} = U L^{-1/2} U^T
 // stored over S.
-__global__ void k_inv_sqrt(View v, double* __restrict__ S) {
+// cond[a] receives lambda_min / lambda_max of the atom's overlap matrix, or -1 when that ratio is not
+// defined (no positive or a non-finite eigenvalue); the host refuses atoms whose orbitals are linearly
+// dependent on the sphere, for which S^(-1/2) does not exist.
+__global__ void k_inv_sqrt(View v, double* __restrict__ S, double* __restrict__ cond) {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= v.natoms) return;
     int M = v.atom_M[a];
@@ -205,6 +208,9 @@ __global__ void k_inv_sqrt(View v, double* __restrict__ S) {
                 }
             }
     }
+    double lmin = A[0][0], lmax = A[0][0];
+    for (int p = 1; p < M; ++p) { lmin = fmin(lmin, A[p][p]); lmax = fmax(lmax, A[p][p]); }
+    cond[a] = (isfinite(lmin) && isfinite(lmax) && lmax > 0.0) ? lmin / lmax : -1.0;
     double il[MAXM];
     for (int p = 0; p < M; ++p) il[p] = 1.0 / sqrt(A[p][p]);
     for (int p = 0; p < M; ++p)
@@ -238,9 +244,9 @@ __global__ void k_lowdin_apply(View v, const double* __restrict__ T) {
     }
 }
 
-cudaError_t launch_lowdin(const View& v, double* work_S, cudaStream_t st) {
+cudaError_t launch_lowdin(const View& v, double* work_S, double* cond, cudaStream_t st) {
     k_overlap<<<v.natoms, CTA, 0, st>>>(v, work_S);
-    k_inv_sqrt<<<(v.natoms + 63) / 64, 64, 0, st>>>(v, work_S);
+    k_inv_sqrt<<<(v.natoms + 63) / 64, 64, 0, st>>>(v, work_S, cond);
     k_lowdin_apply<<<v.ntiles, TILE, 0, st>>>(v, work_S);
     return cudaGetLastError();
 }

@@ -241,6 +241,24 @@ def test_argument_and_order_errors():
     assert e.value.status == dftu.DFTU_ERR_INVALID_ARG
 
 
+def test_linearly_dependent_orbitals_are_refused():
+    """Orbitals that are linearly dependent on their sphere have no S^{-1/2}: the library refuses them
+    at set-up, like the oracle, and accepts the independent p shell on the same seven points."""
+    from tests.test_oracle_pins import degenerate_shell_systems
+    d7, zero, p7 = degenerate_shell_systems()
+    for s in (d7, zero):
+        with pytest.raises(dftu.DftuError) as e:
+            dftu.handle_for_system(s, 2)
+        assert e.value.status == dftu.DFTU_ERR_INVALID_ARG
+        assert "linearly dependent" in str(e.value)
+    h = dftu.handle_for_system(p7, 2)
+    idx, img, phi = h.get_sphere(0)
+    st = O.setup_atoms(p7)[0]
+    assert np.array_equal(idx.astype(np.int64), st["idx"])
+    assert rel(phi, st["phi"]) < 1e-13
+    h.close()
+
+
 def test_allocation_failure_is_reported_and_harmless():
     """A handle sized for 2^30 bands asks for 550 GB in its first band-sized buffer, more than the device
     holds: the set-up returns DFTU_ERR_ALLOC (a failed allocation, nothing launched), and the next

@@ -59,6 +59,32 @@ def test_sphere_boundary_is_inclusive():
     assert int(np.sum(sm["r"] == 2.5)) == 30
 
 
+def degenerate_shell_systems():
+    """Two atoms whose orbitals are linearly dependent on their sphere, and a healthy neighbour case.
+    On an h = 0.5 grid a sphere of radius 0.6 around a grid point holds the point and its six axis
+    neighbours: xy, yz and xz vanish on all seven (and the 3d radial vanishes at the centre), so three
+    of the five d orbitals are zero there.  A radial table of zeros gives S = 0.  The p shell on the
+    same seven points has three independent orbitals (x, y, z along the axes)."""
+    g = synth.Grid((8, 8, 8), (0.5, 0.5, 0.5), periodic=False)
+    one = lambda at, rad: synth.System(g, [at], [rad], np.zeros((1, 3)), np.ones(1), nspin=1)
+    d7 = one(synth.Atom((2.0, 2.0, 2.0), 0, 2, 0.6), synth.hydrogenic_radial(3, 2, 4.0))
+    zero = one(synth.Atom((2.0, 2.0, 2.0), 0, 1, 1.6), synth.Radial(0.01, np.zeros(600)))
+    p7 = one(synth.Atom((2.0, 2.0, 2.0), 0, 1, 0.6), synth.hydrogenic_radial(2, 1, 2.5))
+    return d7, zero, p7
+
+
+def test_lowdin_refuses_linearly_dependent_orbitals():
+    """S^{-1/2} (Sec. III's orthonormal basis) does not exist for dependent orbitals: refused."""
+    d7, zero, p7 = degenerate_shell_systems()
+    assert len(O.sphere_map(d7.grid, d7.atoms[0])["idx"]) == 7
+    for s in (d7, zero):
+        with pytest.raises(ValueError):
+            O.setup_atoms(s)
+    st = O.setup_atoms(p7)[0]
+    assert len(st["idx"]) == 7
+    assert np.allclose(p7.grid.dV * st["phi"].T @ st["phi"], np.eye(3), atol=1e-13)
+
+
 def test_radial_interpolation_exact_on_cubics_and_converges():
     dr = 0.05
     r = np.arange(200) * dr
