@@ -23,7 +23,8 @@
  *     any host memory when the GPU reads pageable memory.  Host-resident states are read and
  *     written by the kernels directly over the host link: only the sphere points move.  Other
  *     pointers are refused with DFTU_ERR_INVALID_ARG; the check is skipped while the stream is
- *     capturing a graph.
+ *     capturing a graph.  The small device inputs (occupations f, the apply coefficient, the vector
+ *     potential A) are checked the same way and may also sit in page-locked host memory.
  *   - psi is the full Bloch function on the cell.  A sphere point at unfolded position r_u folds
  *     to r_w = r_u - T; the gather multiplies psi(r_w) by exp(+i k.T), the scatter by exp(-i k.T).
  *   - Occupation matrices are reported as the paper's n_{mm'} = sum w f <psi|phi_m><phi_m'|psi>.

@@ -622,6 +622,7 @@ dftu_status dftu_occupations(dftu_handle h, const double* f, dftu_stream stream)
     if (!f) return fail(c, DFTU_ERR_INVALID_ARG, "occupations: null f");
     Guard g(c->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!gpu_addressable(c->device, f, st)) return fail(c, DFTU_ERR_INVALID_ARG, "occupations: f is not addressable by this GPU");
     cudaError_t e = launch_nbar(c->v, c->proj_nbands, st);
     if (e == cudaSuccess) e = launch_occupations(c->v, f, c->proj_nbands, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "occupations");
@@ -662,6 +663,7 @@ dftu_status dftu_apply(dftu_handle h, void* psi_out, dftu_prec prec, int nbands,
     strides(c, nbands, ld_band, sk, ss, sn);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (!gpu_addressable(c->device, psi_out, st)) return fail(c, DFTU_ERR_INVALID_ARG, "apply: the states are not addressable by this GPU (device memory of another GPU, or pageable host memory on a device without pageable access)");
+    if (coef && !gpu_addressable(c->device, coef, st)) return fail(c, DFTU_ERR_INVALID_ARG, "apply: coef is not addressable by this GPU");
     cudaError_t e = launch_apply(c->v, psi_out, prec, c->f64_mode, nbands, sk, ss, sn, coef ? coef : c->d_coef_one,
                                  c->d_color_order, c->color_beg, c->variant[prec == DFTU_C64 ? 3 : 2], accumulate ? 1 : 0, st,
                                  c->gauge_on);
@@ -687,6 +689,7 @@ dftu_status dftu_taylor_step(dftu_handle h, void* psi, void* work, dftu_prec pre
     strides(c, nbands, ld_band, sk, ss, sn);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (!gpu_addressable(c->device, psi, st) || !gpu_addressable(c->device, work, st)) return fail(c, DFTU_ERR_INVALID_ARG, "taylor_step: the states are not addressable by this GPU (device memory of another GPU, or pageable host memory on a device without pageable access)");
+    if (!gpu_addressable(c->device, f, st)) return fail(c, DFTU_ERR_INVALID_ARG, "taylor_step: f is not addressable by this GPU");
     const int vp = c->variant[prec == DFTU_C64 ? 1 : 0], va = c->variant[prec == DFTU_C64 ? 3 : 2];
     const bool G = c->gauge_on;
     cudaError_t e = launch_project(c->v, psi, prec, c->f64_mode, nbands, sk, ss, sn, vp, st, G);
@@ -725,6 +728,7 @@ dftu_status dftu_forces(dftu_handle h, const void* const* dpsi, dftu_prec prec, 
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     for (int i = 0; i < 3; ++i)
         if (!gpu_addressable(c->device, dpsi[i], st)) return fail(c, DFTU_ERR_INVALID_ARG, "forces: the states are not addressable by this GPU (device memory of another GPU, or pageable host memory on a device without pageable access)");
+    if (!gpu_addressable(c->device, f, st)) return fail(c, DFTU_ERR_INVALID_ARG, "forces: f is not addressable by this GPU");
     const int64_t gstride = (int64_t)c->nk * c->ns * c->max_bands * c->MT;
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
@@ -754,6 +758,7 @@ dftu_status dftu_set_vector_potential(dftu_handle h, const double* A, dftu_strea
     }
     Guard g(c->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!gpu_addressable(c->device, A, st)) return fail(c, DFTU_ERR_INVALID_ARG, "set_vector_potential: A is not addressable by this GPU");
     cudaError_t e = launch_gauge_phases(c->v, A, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "set_vector_potential");
     c->gauge_on = true;
@@ -778,6 +783,7 @@ dftu_status dftu_hubbard_current(dftu_handle h, const void* psi, dftu_prec prec,
     strides(c, nbands, ld_band, sk, ss, sn);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (!gpu_addressable(c->device, psi, st)) return fail(c, DFTU_ERR_INVALID_ARG, "hubbard_current: the states are not addressable by this GPU (device memory of another GPU, or pageable host memory on a device without pageable access)");
+    if (!gpu_addressable(c->device, f, st)) return fail(c, DFTU_ERR_INVALID_ARG, "hubbard_current: f is not addressable by this GPU");
     const int64_t gstride = (int64_t)c->nk * c->ns * c->max_bands * c->MT;
     View vq = c->v;   // the same states projected onto phi_m d_a (a = x, y, z) in one launch, into the gradient buffer
     vq.phi64 = c->v.phid64;

@@ -128,8 +128,8 @@ dftu_status dftu_batch_bind(dftu_batch b, const void* const* psi, dftu_prec prec
         const int64_t npts = (int64_t)c->grid.n[0] * c->grid.n[1] * c->grid.n[2];
         if (!psi[s] || !f[s] || nbands[s] < 1 || nbands[s] > c->max_bands || ld_band[s] < npts)
             return bfail(b, DFTU_ERR_INVALID_ARG, "batch_bind: system " + std::to_string(s) + " has a null pointer, bad band count or ld_band");
-        if (!gpu_addressable(b->device, psi[s], nullptr))
-            return bfail(b, DFTU_ERR_INVALID_ARG, "batch_bind: the states of system " + std::to_string(s) + " are not addressable by this GPU");
+        if (!gpu_addressable(b->device, psi[s], nullptr) || !gpu_addressable(b->device, f[s], nullptr))
+            return bfail(b, DFTU_ERR_INVALID_ARG, "batch_bind: the states or occupations of system " + std::to_string(s) + " are not addressable by this GPU");
         ProjArgs a{};
         a.psi = psi[s];
         a.nbands = nbands[s];

@@ -243,14 +243,18 @@ class Handle:
             raise ValueError("psi's last dimension is shorter than the grid")
         return prec, nb, psi.shape[3]
 
+    @staticmethod
+    def _f_arg(f: torch.Tensor) -> C.c_void_p:
+        if f.dtype != torch.float64 or not f.is_contiguous() or not (f.is_cuda or f.is_pinned()):
+            raise ValueError("f must be a contiguous float64 CUDA tensor or pinned host tensor")
+        return C.c_void_p(f.data_ptr())
+
     def project(self, psi: torch.Tensor, stream=None):
         prec, nb, ld = self._psi_args(psi)
         self._check(self.lib.dftu_project(self.h, C.c_void_p(psi.data_ptr()), prec, nb, ld, _stream_ptr(stream, self.device)))
 
     def occupations(self, f: torch.Tensor, stream=None):
-        if f.dtype != torch.float64 or not f.is_cuda or not f.is_contiguous():
-            raise ValueError("f must be a contiguous float64 CUDA tensor")
-        self._check(self.lib.dftu_occupations(self.h, C.c_void_p(f.data_ptr()), _stream_ptr(stream, self.device)))
+        self._check(self.lib.dftu_occupations(self.h, self._f_arg(f), _stream_ptr(stream, self.device)))
 
     def acbn0_uj(self, stream=None):
         self._check(self.lib.dftu_acbn0_uj(self.h, _stream_ptr(stream, self.device)))
@@ -259,8 +263,8 @@ class Handle:
         prec, nb, ld = self._psi_args(psi)
         cp = None
         if coef is not None:
-            if coef.dtype != torch.complex128 or not coef.is_cuda:
-                raise ValueError("coef must be a complex128 CUDA tensor")
+            if coef.dtype != torch.complex128 or not (coef.is_cuda or coef.is_pinned()):
+                raise ValueError("coef must be a complex128 CUDA tensor or pinned host tensor")
             cp = C.c_void_p(coef.data_ptr())
         self._check(self.lib.dftu_apply(self.h, C.c_void_p(psi.data_ptr()), prec, nb, ld, cp, 1 if accumulate else 0,
                                         _stream_ptr(stream, self.device)))
@@ -273,14 +277,16 @@ class Handle:
                 raise ValueError("the three gradients must share shape, dtype and layout")
         arr = (C.c_void_p * 3)(*[d.data_ptr() for d in dpsi])
         F = np.zeros((self.natoms, 3))
-        self._check(self.lib.dftu_forces(self.h, arr, prec, nb, ld, C.c_void_p(f.data_ptr()), _dp(F),
+        self._check(self.lib.dftu_forces(self.h, arr, prec, nb, ld, self._f_arg(f), _dp(F),
                                          _stream_ptr(stream, self.device)))
         return F
 
     def set_vector_potential(self, A: Optional[torch.Tensor], stream=None):
-        """Uniform vector potential of the gauge-invariant operator (Sec. V): a float64 CUDA tensor of 3, or None."""
-        if A is not None and (A.dtype != torch.float64 or not A.is_cuda or A.numel() != 3 or not A.is_contiguous()):
-            raise ValueError("A must be a contiguous float64 CUDA tensor of 3 elements")
+        """Uniform vector potential of the gauge-invariant operator (Sec. V): a float64 tensor of 3 on the GPU
+        or in pinned host memory, or None."""
+        if A is not None and (A.dtype != torch.float64 or not (A.is_cuda or A.is_pinned()) or A.numel() != 3
+                              or not A.is_contiguous()):
+            raise ValueError("A must be a contiguous float64 CUDA or pinned host tensor of 3 elements")
         self._A = A   # keep it alive: the phase kernel reads it when it runs
         ptr = C.c_void_p(A.data_ptr()) if A is not None else None
         self._check(self.lib.dftu_set_vector_potential(self.h, ptr, _stream_ptr(stream, self.device)))
@@ -290,7 +296,7 @@ class Handle:
         prec, nb, ld = self._psi_args(psi)
         J = np.zeros(3)
         Jat = np.zeros((self.natoms, 3))
-        self._check(self.lib.dftu_hubbard_current(self.h, C.c_void_p(psi.data_ptr()), prec, nb, ld, C.c_void_p(f.data_ptr()),
+        self._check(self.lib.dftu_hubbard_current(self.h, C.c_void_p(psi.data_ptr()), prec, nb, ld, self._f_arg(f),
                                                   _dp(J), _dp(Jat), _stream_ptr(stream, self.device)))
         return (J, Jat) if per_atom else J
 
@@ -304,10 +310,8 @@ class Handle:
         prec, nb, ld = self._psi_args(psi)
         if work.shape != psi.shape or work.dtype != psi.dtype or not work.is_contiguous():
             raise ValueError("work must match psi")
-        if f.dtype != torch.float64 or not f.is_cuda or not f.is_contiguous():
-            raise ValueError("f must be a contiguous float64 CUDA tensor")
         self._check(self.lib.dftu_taylor_step(self.h, C.c_void_p(psi.data_ptr()), C.c_void_p(work.data_ptr()), prec, nb, ld,
-                                              C.c_void_p(f.data_ptr()), float(dt), int(order), _stream_ptr(stream, self.device)))
+                                              self._f_arg(f), float(dt), int(order), _stream_ptr(stream, self.device)))
 
     # ------------------------------------------------------------------ results
     def _mat_sizes(self):

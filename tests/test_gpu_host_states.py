@@ -71,3 +71,35 @@ def test_pageable_host_states_are_used_or_refused():
         assert np.array_equal(h.projections(nb), p_dev)      # the earlier projections are untouched
     torch.cuda.synchronize()
     h.close()
+
+
+def test_host_occupations_coefficient_and_vector_potential():
+    """The occupations f, the apply coefficient and the vector potential A in page-locked host memory
+    give the device-memory results bit for bit; pageable f is used or refused like pageable states."""
+    s, nb, h, d, host, fd = _setup(torch.complex128)
+    c_dev = torch.tensor([0.3 - 0.1j], dtype=torch.complex128, device="cuda")
+    A_dev = torch.tensor([0.2, -0.1, 0.3], dtype=torch.float64, device="cuda")
+    runs = {}
+    for name, f_, c_, A_ in (("device", fd, c_dev, A_dev),
+                             ("host", fd.cpu().pin_memory(), c_dev.cpu().pin_memory(), A_dev.cpu().pin_memory())):
+        x = d.clone()
+        h.set_vector_potential(None)
+        h.project(x); h.occupations(f_); h.acbn0_uj(); h.apply(x, c_)
+        h.set_vector_potential(A_)
+        h.project(x); h.occupations(f_); h.acbn0_uj(); h.apply(x, c_)
+        torch.cuda.synchronize()
+        runs[name] = (x.cpu(), h.results()["EU"])
+    assert torch.equal(runs["device"][0], runs["host"][0])
+    assert runs["device"][1] == runs["host"][1]
+    assert h.sync_status() == dftu.DFTU_OK
+    h.set_vector_potential(None)
+    h.project(d)
+    fpage = np.ascontiguousarray(fd.cpu().numpy().copy())
+    lib = dftu.load()
+    torch.cuda.synchronize()
+    st = lib.dftu_occupations(h.h, C.c_void_p(fpage.ctypes.data), C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st in (dftu.DFTU_OK, dftu.DFTU_ERR_INVALID_ARG)
+    if st == dftu.DFTU_ERR_INVALID_ARG:
+        assert b"not addressable" in lib.dftu_last_error(h.h)
+    torch.cuda.synchronize()
+    h.close()
