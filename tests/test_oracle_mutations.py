@@ -142,6 +142,15 @@ def _acbn0_nc_without_spin_flip(rho, Pb_rho, V):
     return float(np.real(numU) / np.real(den_u)), float(np.real(numJ) / np.real(den_j)), False
 
 
+def _fll_without_spin_flip_exchange(rho, U, J, noncollinear, nspin=2):
+    """E_ee of Eq. (A1) with the -J/2 spin-flip (off-diagonal spin block) term left out."""
+    ee, dc = ORIG["fll_energy"](rho, U, J, noncollinear, nspin)
+    nb = O.spin_blocks(rho, noncollinear, nspin)
+    d = np.array([[np.diagonal(nb[s, t]) for t in range(2)] for s in range(2)])
+    flip = sum(-0.5 * J * (np.sum(d[s, 1 - s]) * np.sum(d[1 - s, s]) - np.sum(d[s, 1 - s] * d[1 - s, s])) for s in range(2))
+    return ee - float(np.real(flip)), dc
+
+
 # name -> (replacements, pin that must fail, its arguments)
 CASES = {
     "Bloch phase with the wrong sign": (
@@ -240,6 +249,33 @@ CASES = {
         dict(coulomb_integrals=lambda grid, atom, smap: np.transpose(
             ORIG["coulomb_integrals"](grid, atom, smap), (0, 2, 1, 3))),
         P.test_coulomb_integrals_against_slater_integrals, ("p",)),
+    "gauge phase missing from the projection": (
+        dict(project_gauge=lambda system, st, psi, A: ORIG["project"](system, st, psi)),
+        P.test_gauge_operator_equals_literal_definition_on_isolated_box, ()),
+    "gauge scatter with the gather's phase": (
+        dict(apply_gauge=lambda system, st, psi, p, V, A, coef=1.0: ORIG["apply_gauge"](
+            system, st, psi, p, V, -np.asarray(A, dtype=np.float64), coef)),
+        P.test_gauge_operator_equals_literal_definition_on_isolated_box, ()),
+    "current components on the wrong axes": (
+        dict(hubbard_current=lambda *a: ORIG["hubbard_current"](*a)[[1, 2, 0]]),
+        P.test_hubbard_current_is_energy_derivative_in_A, ()),
+    "forces from the gradients of the wrong axes": (
+        dict(hubbard_forces=lambda system, st, psi, dpsi, f, V: ORIG["hubbard_forces"](
+            system, st, psi, [dpsi[1], dpsi[2], dpsi[0]], f, V)),
+        P.test_hubbard_forces_match_finite_difference_of_energy, ()),
+    "Coulomb truncation radius too short": (
+        dict(poisson_box=lambda grid, radius: (ORIG["poisson_box"](grid, radius)[0], 1.0 * radius)),
+        P.test_coulomb_integrals_against_slater_integrals, ("d",)),
+    "unpolarised channel counted once in the energy": (
+        dict(hubbard_energy=lambda rho_s, U, nspin: ORIG["hubbard_energy"](rho_s, U, nspin) / (2 if nspin == 1 else 1)),
+        P.test_dudarev_energy_and_potential_closed_forms_diagonal, ()),
+    "spinor occupations without the k-point weights": (
+        dict(occupations_nc=lambda system, p_atoms, f: ORIG["occupations_nc"](
+            system, p_atoms, f * len(system.wk) * np.asarray(system.wk)[:, None] ** 0)),
+        P.test_noncollinear_reduces_to_collinear_for_spin_pure_spinors, ()),
+    "FLL E_ee without the spin-flip exchange": (
+        dict(fll_energy=_fll_without_spin_flip_exchange),
+        P.test_fll_energy_vanishes_for_integer_occupations, ()),
     "FLL double counting without the m.m term": (
         dict(fll_energy=_fll_without_mm),
         P.test_fll_double_counting_moment_term, ()),
