@@ -55,22 +55,28 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons during the timed region."""
+    """nvidia-smi clocks and throttle reasons during the timed region.  Sampling starts before the region
+    (nvidia-smi takes a moment to start) and every sample carries nvidia-smi's own timestamp; mark() records
+    the region's wall-clock bounds, and only the samples inside them are summarised (all of them when no
+    region was marked, with the count of those inside reported either way)."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 25
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.rows = []
         self.proc = None
+        self.marks = []
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                                          "-lms", str(self.PERIOD_MS)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            time.sleep(0.5)   # let nvidia-smi start sampling before the region begins
         except Exception:
             self.proc = None
 
@@ -78,27 +84,67 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.rows.append([x.strip() for x in line.split(",")])
 
+    def mark(self):
+        """Call right after a device synchronisation at the start and at the end of the timed region."""
+        self.marks.append(time.time())
+
+    @staticmethod
+    def summarize(rows, t0=None, t1=None):
+        """Median SM clock, maximum clock and the throttle reasons seen, over the samples whose timestamp
+        lies in [t0, t1].  Without a region, or when no sample carries a readable timestamp, all samples
+        count; when none falls inside the region, those within 0.1 s of it count, and a note says so."""
+        import datetime
+        parsed = []
+        for r in rows:
+            if len(r) < 10 or not r[2].replace(".", "").isdigit():
+                continue
+            try:
+                ts = datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None
+            parsed.append((ts, r))
+        note = None
+        use = [r for _, r in parsed]
+        if t0 is not None:
+            if not any(ts is not None for ts, _ in parsed):
+                note = "nvidia-smi timestamps unreadable: all samples used"
+            else:
+                inside = [r for ts, r in parsed if ts is not None and t0 <= ts <= t1]
+                near = [r for ts, r in parsed if ts is not None and t0 - 0.1 <= ts <= t1 + 0.1]
+                if inside:
+                    use = inside
+                elif near:
+                    use, note = near, "no sample inside the timed region: samples within 0.1 s of it used"
+                else:
+                    note = "no sample near the timed region: all samples used"
+        sm = [float(r[2]) for r in use]
+        mx = [float(r[3]) for r in use if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in use:
+            for n, val in zip(names, r[6:10]):
+                if val.lower().startswith("active"):
+                    reasons.add(n)
+        out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+               "reasons": sorted(reasons), "samples": len(sm), "sample_period_ms": ClockSampler.PERIOD_MS}
+        if t0 is not None:
+            out["region_s"] = round(t1 - t0, 3)
+        if note:
+            out["note"] = note
+        return out
+
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        time.sleep(0.25)
+        time.sleep(0.1)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = set()
-        for r in self.rows:
-            if len(r) < 9:
-                continue
-            for n, val in zip(names, r[5:9]):
-                if val.lower().startswith("active"):
-                    reasons.add(n)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        if len(self.marks) >= 2:
+            return self.summarize(self.rows, self.marks[0], self.marks[-1])
+        return self.summarize(self.rows)
 
 
 def max_over_ranks(values, device):
@@ -172,7 +218,7 @@ def run_ours(args):
         h.acbn0_uj()
         h.apply(out)
 
-    def timed(x, out, steps, warmup):
+    def timed(x, out, steps, warmup, sampler=None):
         for _ in range(warmup):
             step(x, out)
         torch.cuda.synchronize()
@@ -183,6 +229,8 @@ def run_ours(args):
                torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         start = torch.cuda.Event(enable_timing=True)
         end = torch.cuda.Event(enable_timing=True)
+        if sampler is not None:
+            sampler.mark()
         start.record(stream)
         for i in range(steps):
             e0, e1, e2, e3, e4 = ev[i]
@@ -197,6 +245,8 @@ def run_ours(args):
             e4.record(stream)
         end.record(stream)
         torch.cuda.synchronize()
+        if sampler is not None:
+            sampler.mark()
         total = start.elapsed_time(end)
         proj = [e[0].elapsed_time(e[1]) for e in ev]
         small = [e[1].elapsed_time(e[2]) for e in ev]
@@ -218,7 +268,7 @@ def run_ours(args):
         h.project(psi); h.occupations(f); h.acbn0_uj()
     clocks = ClockSampler(local)
     clocks.start()
-    ms64, proj64, small64, app64 = timed(psi, hpsi, args.steps, args.warmup)
+    ms64, proj64, small64, app64 = timed(psi, hpsi, args.steps, args.warmup, sampler=clocks)
     clk = clocks.stop()
     del psi, hpsi
     torch.cuda.empty_cache()
@@ -442,10 +492,12 @@ def run_rt(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(0)
     clocks.start()
+    clocks.mark()
     e0.record()
     g.replay()
     e1.record()
     torch.cuda.synchronize()
+    clocks.mark()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.rt_steps
     n1 = (psi.abs() ** 2).sum(-1).double() * s.grid.dV
@@ -525,7 +577,9 @@ def run_molecules(args):
     allidx = list(range(len(systems)))
     clocks = ClockSampler(0)
     clocks.start()
+    clocks.mark()
     ms_b = time_it(batched, args.steps, args.warmup)
+    clocks.mark()
     clk = clocks.stop()
     ms_1 = time_it(lambda: one_by_one(allidx, psis), max(1, args.steps // 2), 1)
     batch.close()
@@ -598,7 +652,9 @@ def run_nc(args):
 
     clocks = ClockSampler(0)
     clocks.start()
+    clocks.mark()
     ms64 = t(psi, hpsi)
+    clocks.mark()
     clk = clocks.stop()
     ms32 = t(psi32, hpsi32)
     S = _sphere_bytes(h, len(s.atoms))
@@ -669,7 +725,9 @@ def run_gauge(args):
     ms_plain, pr_plain, ap_plain = timed(psi, hpsi, False, args.steps, args.warmup)
     clocks = ClockSampler(0)
     clocks.start()
+    clocks.mark()
     ms_g, pr_g, ap_g = timed(psi, hpsi, True, args.steps, args.warmup)
+    clocks.mark()
     clk = clocks.stop()
     # Hubbard current: three projections onto the displaced orbitals + the contraction, blocking
     h.set_vector_potential(A); h.project(psi); h.occupations(f); h.acbn0_uj()
