@@ -54,6 +54,41 @@ def measured_peaks():
     return 6800.0, "fallback (6.8 TB/s, profiling recipe)"
 
 
+def smi_gpu_id(ordinal: int, uuid=None, visible=None) -> str:
+    """The nvidia-smi -i argument that names CUDA device `ordinal`.  nvidia-smi numbers GPUs by its own
+    (PCI) enumeration and ignores CUDA_VISIBLE_DEVICES, so a CUDA ordinal is not an nvidia-smi index when
+    only some GPUs are visible.  The device's UUID names it unambiguously; without one, the ordinal's
+    entry of CUDA_VISIBLE_DEVICES (an index or a UUID) is used, and the ordinal itself only when that
+    variable is unset."""
+    if uuid:
+        u = str(uuid).strip()
+        return u if u.startswith(("GPU-", "MIG-")) else "GPU-" + u
+    if visible:
+        entries = [x.strip() for x in visible.split(",") if x.strip()]
+        if 0 <= ordinal < len(entries):
+            return entries[ordinal]
+    return str(ordinal)
+
+
+def resolve_smi_id(ordinal: int) -> str:
+    uuid = None
+    try:
+        import torch
+        uuid = str(torch.cuda.get_device_properties(ordinal).uuid)
+    except Exception:
+        uuid = None
+    visible = os.environ.get("CUDA_VISIBLE_DEVICES")
+    for cand in (smi_gpu_id(ordinal, uuid, visible), smi_gpu_id(ordinal, None, visible)):
+        try:
+            r = subprocess.run(["nvidia-smi", "-i", cand, "--query-gpu=uuid", "--format=csv,noheader"],
+                               capture_output=True, text=True, timeout=20)
+            if r.returncode == 0 and r.stdout.strip():
+                return cand
+        except Exception:
+            pass
+    return smi_gpu_id(ordinal, uuid, visible)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons during the timed region.  Sampling starts before the region
     (nvidia-smi takes a moment to start) and every sample carries nvidia-smi's own timestamp; mark() records
@@ -64,15 +99,15 @@ class ClockSampler:
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
     PERIOD_MS = 25
 
-    def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
+    def __init__(self, device_ordinal: int):
+        self.gpu = resolve_smi_id(device_ordinal)
         self.rows = []
         self.proc = None
         self.marks = []
 
     def start(self):
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu, f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
                                           "-lms", str(self.PERIOD_MS)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -142,9 +177,9 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        if len(self.marks) >= 2:
-            return self.summarize(self.rows, self.marks[0], self.marks[-1])
-        return self.summarize(self.rows)
+        out = self.summarize(self.rows, self.marks[0], self.marks[-1]) if len(self.marks) >= 2 else self.summarize(self.rows)
+        out["gpu"] = self.gpu
+        return out
 
 
 def max_over_ranks(values, device):

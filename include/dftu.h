@@ -248,8 +248,11 @@ dftu_status dftu_forces(dftu_handle h, const void* const* dpsi, dftu_prec prec, 
  *   phase  [npts] complex128 factor of each point (e.g. exp(+i k.T) of its lattice image), device, or NULL for 1.
  *   phi    [npts][M] orbital values (FP64), device.
  *   p_out  [nbands][M] complex128 result, device:  p[n][m] = dV sum_j phi[j][m] phase[j] psi[n][idx[j]], in FP64.
- * Errors: DFTU_ERR_INVALID_ARG for null pointers, M outside 1..7, or ceil(npts/512)*nbands*M above
- * 524288 (the scratch size); DFTU_ERR_CUDA if a launch fails.  The first call on a device looks up the
+ * Errors: DFTU_ERR_INVALID_ARG for null pointers, a pointer this GPU cannot address (checked as for the
+ * states of the handle calls), M outside 1..7, or ceil(npts/512)*nbands*M above 524288 (the scratch
+ * size); DFTU_ERR_CUDA if a launch fails (an error the caller left pending is neither reported nor
+ * cleared).  A grid index outside [0, ld_band) is never read: the projections of that call then come
+ * out NaN.  The first call on a device looks up the
  * scratch array's device address (once per device), so make that first call before any stream
  * capture.  Every call uses the same scratch: calls that overlap on the GPU (other streams, other
  * threads) race and give wrong results; calls ordered on one stream are safe. */

@@ -24,7 +24,9 @@ static __device__ __align__(256) double2 g_na_scratch[NA_SCRATCH_ELEMS];
 std::mutex g_na_mutex;
 double2* g_na_ptr[NA_MAXDEV] = {nullptr};
 
-// partial[tile][band][m] = dV sum_{j in tile} phi[j][m] phase[j] psi[band][idx[j]]   (FP64)
+// partial[tile][band][m] = dV sum_{j in tile} phi[j][m] phase[j] psi[band][idx[j]]   (FP64).
+// A grid index outside [0, ld) is never read: the tile then writes NaN partial sums for every band,
+// so the projections of the call come out NaN.
 template <typename T>
 __global__ void __launch_bounds__(NA_CTA) k_na_tiles(const T* __restrict__ psi, int nbands, int64_t ld,
                                                      const int* __restrict__ idx, const double2* __restrict__ phase,
@@ -33,15 +35,22 @@ __global__ void __launch_bounds__(NA_CTA) k_na_tiles(const T* __restrict__ psi, 
     __shared__ int s_idx[NA_TILE];
     __shared__ double2 s_ph[NA_TILE];
     __shared__ double s_phi[NA_TILE * dftu::MAXM];
+    __shared__ int s_bad;
     const int tile = blockIdx.x;
     const int p0 = tile * NA_TILE;
     const int np = min(NA_TILE, npts - p0);
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
     for (int i = threadIdx.x; i < np; i += NA_CTA) {
-        s_idx[i] = idx[p0 + i];
+        const int g = idx[p0 + i];
+        const bool ok = g >= 0 && (int64_t)g < ld;
+        if (!ok) s_bad = 1;
+        s_idx[i] = ok ? g : 0;
         s_ph[i] = phase ? phase[p0 + i] : make_double2(1.0, 0.0);
     }
     for (int e = threadIdx.x; e < np * M; e += NA_CTA) s_phi[e] = phi[(int64_t)p0 * M + e];
     __syncthreads();
+    const bool bad = s_bad != 0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int band = warp; band < nbands; band += NA_CTA / 32) {
         const T* row = psi + (int64_t)band * ld;
@@ -64,9 +73,12 @@ __global__ void __launch_bounds__(NA_CTA) k_na_tiles(const T* __restrict__ psi, 
                 im[m] += __shfl_xor_sync(0xffffffffu, im[m], off);
             }
         }
-        if (lane == 0)
+        if (lane == 0) {
+            const double nan = __longlong_as_double(0x7FF8000000000000LL);
             for (int m = 0; m < M; ++m)
-                part[((int64_t)tile * nbands + band) * M + m] = make_double2(dV * re[m], dV * im[m]);
+                part[((int64_t)tile * nbands + band) * M + m] =
+                    bad ? make_double2(nan, nan) : make_double2(dV * re[m], dV * im[m]);
+        }
     }
 }
 
@@ -109,16 +121,28 @@ extern "C" dftu_status dftu_project_sphere_noalloc(const void* psi, dftu_prec pr
     double2* part = scratch_for_current_device(dev);
     if (!part) return DFTU_ERR_CUDA;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (!dftu::gpu_addressable(dev, psi, st)) return DFTU_ERR_INVALID_ARG;
-    if (prec == DFTU_C128)
-        k_na_tiles<double2><<<ntiles, NA_CTA, 0, st>>>(static_cast<const double2*>(psi), nbands, ld_band, idx,
-                                                        reinterpret_cast<const double2*>(phase), phi, npts, M, dV, part);
-    else
-        k_na_tiles<float2><<<ntiles, NA_CTA, 0, st>>>(static_cast<const float2*>(psi), nbands, ld_band, idx,
-                                                       reinterpret_cast<const double2*>(phase), phi, npts, M, dV, part);
-    if (cudaGetLastError() != cudaSuccess) return DFTU_ERR_CUDA;
-    int n = nbands * M;
-    k_na_reduce<<<(n + 255) / 256, 256, 0, st>>>(part, ntiles, nbands, M, reinterpret_cast<double2*>(p_out));
-    if (cudaGetLastError() != cudaSuccess) return DFTU_ERR_CUDA;
+    // every operand must be memory this GPU can address (a pageable host array would fault the kernel)
+    if (!dftu::gpu_addressable(dev, psi, st) || !dftu::gpu_addressable(dev, idx, st) || !dftu::gpu_addressable(dev, phi, st) ||
+        !dftu::gpu_addressable(dev, p_out, st) || (phase && !dftu::gpu_addressable(dev, phase, st)))
+        return DFTU_ERR_INVALID_ARG;
+    // Launch errors are taken from the launch calls themselves, so an unrelated error the caller left
+    // pending is neither reported as ours nor cleared.
+    const double2* ph = reinterpret_cast<const double2*>(phase);
+    int nt = ntiles;
+    void* tile_args[] = {(void*)&psi, (void*)&nbands, (void*)&ld_band, (void*)&idx, (void*)&ph,
+                         (void*)&phi, (void*)&npts, (void*)&M, (void*)&dV, (void*)&part};
+    const void* fn = (prec == DFTU_C128) ? reinterpret_cast<const void*>(&k_na_tiles<double2>)
+                                         : reinterpret_cast<const void*>(&k_na_tiles<float2>);
+    cudaError_t e = cudaLaunchKernel(fn, dim3(ntiles), dim3(NA_CTA), tile_args, 0, st);
+    if (e == cudaSuccess) {
+        double2* p = reinterpret_cast<double2*>(p_out);
+        void* red_args[] = {(void*)&part, (void*)&nt, (void*)&nbands, (void*)&M, (void*)&p};
+        const int n = nbands * M;
+        e = cudaLaunchKernel(reinterpret_cast<const void*>(&k_na_reduce), dim3((n + 255) / 256), dim3(256), red_args, 0, st);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();   // the failed launch is reported here, not left for the caller's next check
+        return DFTU_ERR_CUDA;
+    }
     return DFTU_OK;
 }

@@ -37,3 +37,17 @@ def test_fallbacks_without_a_region_or_without_samples_inside_it():
     assert far["samples"] == 2 and "all samples" in far["note"]
     no_ts = [["?", *r[1:]] for r in rows if len(r) == 10]
     assert "unreadable" in bench.ClockSampler.summarize(no_ts, t0, t0 + 1.0)["note"]
+
+
+def test_smi_id_names_the_cuda_device_not_its_ordinal():
+    # the UUID wins over everything, with or without its "GPU-" prefix
+    assert bench.smi_gpu_id(0, "5f0b1c2d-aaaa-bbbb-cccc-0123456789ab", "3") == "GPU-5f0b1c2d-aaaa-bbbb-cccc-0123456789ab"
+    assert bench.smi_gpu_id(0, "GPU-abc", None) == "GPU-abc"
+    assert bench.smi_gpu_id(0, "MIG-abc", None) == "MIG-abc"
+    # without a UUID: the ordinal's entry of CUDA_VISIBLE_DEVICES (an nvidia-smi index or a UUID)
+    assert bench.smi_gpu_id(0, None, "3") == "3"
+    assert bench.smi_gpu_id(1, None, "5, 2") == "2"
+    assert bench.smi_gpu_id(0, None, "GPU-1234") == "GPU-1234"
+    # only with no mapping at all is the ordinal used
+    assert bench.smi_gpu_id(2, None, None) == "2"
+    assert bench.smi_gpu_id(4, None, "1,2") == "4"
