@@ -179,11 +179,17 @@ dftu_status dftu_apply(dftu_handle h, void* psi_out, dftu_prec prec, int nbands,
 
 /* One real-time step with the adiabatic Hubbard potential (Sec. V, Eq. 15): occupations, U and J and
  * V_U are rebuilt from the incoming psi (f: device occupations as for dftu_occupations) and held fixed,
- * then psi <- sum_{j=0}^{order} (-i dt V_U)^j / j! psi, one term at a time: term_j = (-i dt/j) V_U term_{j-1}
- * is written to `work` (same layout as psi; only its sphere points are used) and added to psi.
- * order <= 8.  Only the Hubbard term of the Hamiltonian is propagated (the paper does not name its
- * propagator; 4th-order Taylor with dt = 0.01 a.u. is the workload's choice).  Launches only, no host
- * synchronisation and no allocation: a CUDA graph can capture it. */
+ * then psi <- sum_{j=0}^{order} (-i dt V_U)^j / j! psi.  order <= 8.  Only the Hubbard term of the
+ * Hamiltonian is propagated (the paper does not name its propagator; 4th-order Taylor with dt = 0.01 a.u.
+ * is the workload's choice).
+ * Every term lies in the span of the scattered orbitals, term_j = scatter(a_j), so the step is computed
+ * there: a_1 = c_1 V p(psi), a_j = c_j V O a_{j-1} with c_j = -i dt / j and O the overlap of the gathered
+ * with the scattered orbitals (the identity on each atom's own points after the Loewdin step, plus the
+ * blocks of overlapping spheres and self-overlapping images, built by dftu_setup_atoms), then
+ * psi += scatter(sum_j a_j): one projection and one apply of the states per step, the same polynomial in
+ * V_U as term-by-term on the grid.  work is not used (it may be NULL; if given it must differ from psi).
+ * Afterwards the handle's projections, occupations, U, J and V are those of the incoming psi.
+ * Launches only, no host synchronisation and no allocation: a CUDA graph can capture it. */
 dftu_status dftu_taylor_step(dftu_handle h, void* psi, void* work, dftu_prec prec, int nbands, int64_t ld_band,
                              const double* f, double dt, int order, dftu_stream stream);
 
@@ -259,6 +265,26 @@ dftu_status dftu_forces(dftu_handle h, const void* const* dpsi, dftu_prec prec, 
 dftu_status dftu_project_sphere_noalloc(const void* psi, dftu_prec prec, int nbands, int64_t ld_band,
                                         const int32_t* idx, const double* phase, const double* phi, int npts,
                                         int M, double dV, double* p_out, dftu_stream stream);
+
+/* ---- Several GPUs: occupation sums over disjoint parts of the (k, band) set -----------------------
+ * Eq. (4) and Eq. (8) are sums over k-points and bands of w_k f |p><p| (Pbar with the per-band factor Nbar
+ * of Eq. 9, which needs only the projections of that band), so ranks that each hold a disjoint part of the
+ * (k, band) set -- every rank a handle with its own k-points (keeping their weights in the whole set) and
+ * its own bands and occupations -- form partial sums with dftu_project + dftu_occupations, add them over
+ * the ranks (one allreduce of dftu_occupation_elems doubles), and write the totals back before
+ * dftu_acbn0_uj, which then gives every rank the U, J, E_U and potential of the whole set; each rank's
+ * dftu_apply works on its own states.  The paper's code is single-process; this is the exchange step of
+ * the sums it defines.
+ *
+ * dftu_occupation_elems: the number of doubles of the sums (rho = n^T then Pbar, interleaved complex, in
+ *   the library's internal order; the caller only adds them elementwise).  0 before dftu_setup_atoms.
+ * dftu_export_occupations: copy this handle's sums of the last dftu_occupations to out (device or page-
+ *   locked host memory, dftu_occupation_elems doubles), asynchronously on stream.
+ * dftu_import_occupations: overwrite the handle's sums with in (same layout, e.g. the allreduced totals);
+ *   dftu_acbn0_uj may follow.  Asynchronous on stream. */
+int64_t dftu_occupation_elems(dftu_handle h);
+dftu_status dftu_export_occupations(dftu_handle h, double* out, dftu_stream stream);
+dftu_status dftu_import_occupations(dftu_handle h, const double* in, dftu_stream stream);
 
 /* ---- Batches of independent systems -------------------------------------------------------------
  * Many small systems (e.g. molecules with their own isolated grids) in one context: every member is an

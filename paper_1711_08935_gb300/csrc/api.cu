@@ -2,7 +2,9 @@
 // geometry set-up (sphere membership on the device, point ordering, tiling and apply colouring on the
 // host), buffer ownership, and the asynchronous launches of the hot path.
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <map>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -439,8 +441,8 @@ dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, 
     if (e == cudaSuccess) e = dalloc(c, &v.phid_hi, (size_t)3 * phi_off);
     if (e == cudaSuccess) e = dalloc(c, &v.phid_lo, (size_t)3 * phi_off);
     if (e == cudaSuccess) e = dalloc(c, &v.nbar, (size_t)rowsN * c->max_bands * nspecies);
-    if (e == cudaSuccess) e = dalloc(c, &v.rho, (size_t)mat);
-    if (e == cudaSuccess) e = dalloc(c, &v.pbar, (size_t)mat);
+    if (e == cudaSuccess) e = dalloc(c, &v.rho, (size_t)2 * mat);   // rho, then Pbar: one block for the sharded sums
+    if (e == cudaSuccess) v.pbar = v.rho + mat;
     if (e == cudaSuccess) e = dalloc(c, &v.occ_part, (size_t)natoms * 2 * OCC_SPLIT * 2 * OCC_MAXP);
     if (e == cudaSuccess) e = dalloc(c, &v.occ_count, (size_t)natoms * 2);
     if (e == cudaSuccess) e = cudaMemset(v.occ_count, 0, (size_t)natoms * 2 * sizeof(int));
@@ -469,6 +471,80 @@ dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, 
             return fail(c, DFTU_ERR_INVALID_ARG, "setup_atoms: the orbitals of atom " + std::to_string(a) +
                                                  " are linearly dependent on its sphere (overlap eigenvalue ratio " +
                                                  std::to_string(hcond[a]) + ")");
+    // ---- overlap blocks of the scattered and gathered orbitals (used by the real-time step) ----
+    {
+        std::vector<double> phi_h((size_t)phi_off);
+        e = cudaMemcpy(phi_h.data(), v.phi64, (size_t)phi_off * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, "setup_atoms: orbitals to host");
+        const int64_t S = c->S;
+        std::vector<int> pt_atom((size_t)S), pt_seg((size_t)S);
+        for (const Tile& t : c->tiles)
+            for (int i = 0; i < t.np; ++i) { pt_atom[t.p0 + i] = t.atom; pt_seg[t.p0 + i] = t.seg; }
+        std::vector<std::pair<int, int64_t>> by_idx((size_t)S);
+        for (int64_t p = 0; p < S; ++p) by_idx[p] = {pt_idx[p], p};
+        std::sort(by_idx.begin(), by_idx.end());
+        // key: (I, J, dTx, dTy, dTz) -> M_I x M_J values
+        std::map<std::array<int, 5>, std::vector<double>> blocks;
+        const double dV = v.dV;
+        auto orb = [&](int64_t p) { const int a = pt_atom[p]; return phi_h.data() + c->atom_phi0[a] + (p - c->atom_p0[a]) * c->M[a]; };
+        for (size_t g0 = 0; g0 < by_idx.size();) {
+            size_t g1 = g0 + 1;
+            while (g1 < by_idx.size() && by_idx[g1].first == by_idx[g0].first) ++g1;
+            for (size_t x = g0; x < g1; ++x)
+                for (size_t y = g0; y < g1; ++y) {
+                    const int64_t pa = by_idx[x].second, pb = by_idx[y].second;
+                    const int I = pt_atom[pa], J = pt_atom[pb];
+                    const int* Ta = &seg_T[3 * pt_seg[pa]];
+                    const int* Tb = &seg_T[3 * pt_seg[pb]];
+                    std::vector<double>& B = blocks[{I, J, Ta[0] - Tb[0], Ta[1] - Tb[1], Ta[2] - Tb[2]}];
+                    const int MI = c->M[I], MJ = c->M[J];
+                    if (B.empty()) B.assign((size_t)MI * MJ, 0.0);
+                    const double* fa = orb(pa);
+                    const double* fb = orb(pb);
+                    for (int m = 0; m < MI; ++m)
+                        for (int q = 0; q < MJ; ++q) B[(size_t)m * MJ + q] += dV * fa[m] * fb[q];
+                }
+            g0 = g1;
+        }
+        std::vector<int> rowptr(natoms + 1, 0), bJ;
+        std::vector<int64_t> boff;
+        std::vector<double> bdata, bD, bDg;
+        for (const auto& kv : blocks) {
+            const auto& key = kv.first;
+            ++rowptr[key[0] + 1];
+            bJ.push_back(key[1]);
+            boff.push_back((int64_t)bdata.size());
+            bdata.insert(bdata.end(), kv.second.begin(), kv.second.end());
+            for (int d = 0; d < 3; ++d) {
+                const double Ld = G.periodic ? G.n[d] * G.h[d] : 0.0;
+                const double Dd = key[2 + d] * Ld;
+                bD.push_back(Dd);
+                bDg.push_back(Dd - (atoms[key[0]].pos[d] - atoms[key[1]].pos[d]));
+            }
+        }
+        for (int a = 0; a < natoms; ++a) rowptr[a + 1] += rowptr[a];
+        std::vector<int> orb_atom(MT);
+        for (int a = 0; a < natoms; ++a)
+            for (int m = 0; m < c->M[a]; ++m) orb_atom[c->moff[a] + m] = a;
+        int *d_rp = nullptr, *d_bJ = nullptr, *d_oa = nullptr;
+        int64_t* d_boff = nullptr;
+        double *d_bdata = nullptr, *d_bD = nullptr, *d_bDg = nullptr;
+        e = upload(c, &d_rp, rowptr);
+        if (e == cudaSuccess) e = upload(c, &d_bJ, bJ);
+        if (e == cudaSuccess) e = upload(c, &d_boff, boff);
+        if (e == cudaSuccess) e = upload(c, &d_bdata, bdata);
+        if (e == cudaSuccess) e = upload(c, &d_bD, bD);
+        if (e == cudaSuccess) e = upload(c, &d_bDg, bDg);
+        if (e == cudaSuccess) e = upload(c, &d_oa, orb_atom);
+        if (e == cudaSuccess) e = dalloc(c, &v.blk_phase, (size_t)c->nk * std::max<size_t>(1, bJ.size()));
+        if (e == cudaSuccess) e = dalloc(c, &v.cv, (size_t)rowsP * c->max_bands * MT);
+        if (e == cudaSuccess) e = dalloc(c, &v.gaugeA, 3);
+        if (e == cudaSuccess) e = cudaMemset(v.gaugeA, 0, 3 * sizeof(double));
+        if (e != cudaSuccess) return cuda_fail(c, e, "setup_atoms: overlap blocks");
+        v.nblk = (int)bJ.size();
+        v.blk_rowptr = d_rp; v.blk_J = d_bJ; v.blk_off = d_boff; v.blk_data = d_bdata; v.blk_D = d_bD; v.blk_Dg = d_bDg;
+        v.orb_atom = d_oa;
+    }
     if (npts_out)
         for (int a = 0; a < natoms; ++a) npts_out[a] = c->npts[a];
     c->atoms_ready = true;
@@ -664,9 +740,10 @@ dftu_status dftu_apply(dftu_handle h, void* psi_out, dftu_prec prec, int nbands,
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (!gpu_addressable(c->device, psi_out, st)) return fail(c, DFTU_ERR_INVALID_ARG, "apply: the states are not addressable by this GPU (device memory of another GPU, or pageable host memory on a device without pageable access)");
     if (coef && !gpu_addressable(c->device, coef, st)) return fail(c, DFTU_ERR_INVALID_ARG, "apply: coef is not addressable by this GPU");
-    cudaError_t e = launch_apply(c->v, psi_out, prec, c->f64_mode, nbands, sk, ss, sn, coef ? coef : c->d_coef_one,
-                                 c->d_color_order, c->color_beg, c->variant[prec == DFTU_C64 ? 3 : 2], accumulate ? 1 : 0, st,
-                                 c->gauge_on);
+    cudaError_t e = launch_coefvec(c->v, nbands, st);
+    if (e == cudaSuccess)
+        e = launch_apply(c->v, psi_out, prec, c->f64_mode, nbands, sk, ss, sn, coef ? coef : c->d_coef_one, c->d_color_order,
+                         c->color_beg, c->variant[prec == DFTU_C64 ? 3 : 2], accumulate ? 1 : 0, st, c->gauge_on);
     if (e != cudaSuccess) return cuda_fail(c, e, "apply");
     c->last_stream = st;
     return DFTU_OK;
@@ -678,7 +755,7 @@ dftu_status dftu_taylor_step(dftu_handle h, void* psi, void* work, dftu_prec pre
     Ctx* c = reinterpret_cast<Ctx*>(h);
     if (!c) return DFTU_ERR_INVALID_ARG;
     if (!c->atoms_ready) return fail(c, DFTU_ERR_NOT_READY, "taylor_step: call dftu_setup_atoms first");
-    if (!psi || !work || psi == work || !f || (prec != DFTU_C128 && prec != DFTU_C64) || !valid_stride_args(c, nbands, ld_band) ||
+    if (!psi || psi == work || !f || (prec != DFTU_C128 && prec != DFTU_C64) || !valid_stride_args(c, nbands, ld_band) ||
         order < 1 || order > MAX_TAYLOR || !std::isfinite(dt))
         return fail(c, DFTU_ERR_INVALID_ARG, "taylor_step: null or aliased buffers, bad precision, band count, order or dt");
     for (size_t a = 0; a < c->atoms.size(); ++a)
@@ -688,7 +765,7 @@ dftu_status dftu_taylor_step(dftu_handle h, void* psi, void* work, dftu_prec pre
     int64_t sk, ss, sn;
     strides(c, nbands, ld_band, sk, ss, sn);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (!gpu_addressable(c->device, psi, st) || !gpu_addressable(c->device, work, st)) return fail(c, DFTU_ERR_INVALID_ARG, "taylor_step: the states are not addressable by this GPU (device memory of another GPU, or pageable host memory on a device without pageable access)");
+    if (!gpu_addressable(c->device, psi, st)) return fail(c, DFTU_ERR_INVALID_ARG, "taylor_step: the states are not addressable by this GPU (device memory of another GPU, or pageable host memory on a device without pageable access)");
     if (!gpu_addressable(c->device, f, st)) return fail(c, DFTU_ERR_INVALID_ARG, "taylor_step: f is not addressable by this GPU");
     const int vp = c->variant[prec == DFTU_C64 ? 1 : 0], va = c->variant[prec == DFTU_C64 ? 3 : 2];
     const bool G = c->gauge_on;
@@ -697,14 +774,10 @@ dftu_status dftu_taylor_step(dftu_handle h, void* psi, void* work, dftu_prec pre
     if (e == cudaSuccess) e = launch_occupations(c->v, f, nbands, st);
     if (e == cudaSuccess) e = launch_acbn0(c->v, st);
     if (e == cudaSuccess) e = launch_taylor_coefs(dt, order, c->d_taylor, st);
-    for (int j = 1; j <= order && e == cudaSuccess; ++j) {
-        const double* cj = c->d_taylor + 2 * (j - 1);
-        // term_j = (-i dt / j) V_U term_{j-1}, from the projections of term_{j-1} held by the handle
-        e = launch_apply(c->v, work, prec, c->f64_mode, nbands, sk, ss, sn, cj, c->d_color_order, c->color_beg, va, 0, st, G);
-        if (e == cudaSuccess)
-            e = launch_apply(c->v, psi, prec, c->f64_mode, nbands, sk, ss, sn, cj, c->d_color_order, c->color_beg, va, 1, st, G);
-        if (e == cudaSuccess && j < order) e = launch_project(c->v, work, prec, c->f64_mode, nbands, sk, ss, sn, vp, st, G);
-    }
+    // the terms' coefficients in the span of the orbitals, then one scatter of their sum onto psi
+    if (e == cudaSuccess) e = launch_taylor_cv(c->v, nbands, order, c->d_taylor, G, st);
+    if (e == cudaSuccess)
+        e = launch_apply(c->v, psi, prec, c->f64_mode, nbands, sk, ss, sn, c->d_coef_one, c->d_color_order, c->color_beg, va, 1, st, G);
     if (e != cudaSuccess) return cuda_fail(c, e, "taylor_step");
     c->last_stream = st;
     c->proj_ready = c->occ_ready = c->pot_ready = true;
@@ -863,6 +936,43 @@ dftu_status dftu_get_results(dftu_handle h, double* n_out, double* U, double* J,
     if (e == cudaSuccess && EU_atom) e = cudaMemcpy(EU_atom, c->v.E, na * sizeof(double), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && EU_total) e = cudaMemcpy(EU_total, c->v.Etot, sizeof(double), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "get_results");
+    return DFTU_OK;
+}
+
+int64_t dftu_occupation_elems(dftu_handle h) {
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c || !c->atoms_ready) return 0;
+    return (int64_t)4 * c->mat_total;
+}
+
+dftu_status dftu_export_occupations(dftu_handle h, double* out, dftu_stream stream) {
+    NvtxRange nvtx_range("dftu_export_occupations");
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c) return DFTU_ERR_INVALID_ARG;
+    if (!c->occ_ready) return fail(c, DFTU_ERR_NOT_READY, "export_occupations: call dftu_occupations first");
+    if (!out) return fail(c, DFTU_ERR_INVALID_ARG, "export_occupations: null output");
+    Guard g(c->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!gpu_addressable(c->device, out, st)) return fail(c, DFTU_ERR_INVALID_ARG, "export_occupations: the output is not addressable by this GPU");
+    cudaError_t e = cudaMemcpyAsync(out, c->v.rho, (size_t)2 * c->mat_total * sizeof(double2), cudaMemcpyDefault, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "export_occupations");
+    c->last_stream = st;
+    return DFTU_OK;
+}
+
+dftu_status dftu_import_occupations(dftu_handle h, const double* in, dftu_stream stream) {
+    NvtxRange nvtx_range("dftu_import_occupations");
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c) return DFTU_ERR_INVALID_ARG;
+    if (!c->atoms_ready) return fail(c, DFTU_ERR_NOT_READY, "import_occupations: call dftu_setup_atoms first");
+    if (!in) return fail(c, DFTU_ERR_INVALID_ARG, "import_occupations: null input");
+    Guard g(c->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!gpu_addressable(c->device, in, st)) return fail(c, DFTU_ERR_INVALID_ARG, "import_occupations: the input is not addressable by this GPU");
+    cudaError_t e = cudaMemcpyAsync(c->v.rho, in, (size_t)2 * c->mat_total * sizeof(double2), cudaMemcpyDefault, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "import_occupations");
+    c->last_stream = st;
+    c->occ_ready = true;
     return DFTU_OK;
 }
 

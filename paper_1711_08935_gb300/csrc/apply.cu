@@ -312,7 +312,6 @@ __device__ __forceinline__ void apply_item(const View& v, const ApplyArgs& a, in
     const int bl = (threadIdx.x >> 5) * BPW + lane / Q;
     const int q = lane & (Q - 1);
     const int mo = v.atom_moff[t.atom];
-    const int64_t vo = v.atom_mat_off[t.atom];
     for (int g = 0; g < NBG; ++g) {
         const int band0 = (chunk * NBG + g) * BPC;
         if (band0 >= a.nbands) break;
@@ -322,27 +321,8 @@ __device__ __forceinline__ void apply_item(const View& v, const ApplyArgs& a, in
             int band = band0 + cb;
             double2 c = make_double2(0.0, 0.0);
             if (band < a.nbands) {
-                double re = 0.0, im = 0.0;
-                if (!v.noncollinear) {
-                    const double2* Vm = v.V + vo + (int64_t)s * M * M + m * M;
-                    const double2* pr = v.p + ((int64_t)ks * v.max_bands + band) * v.MT + mo;
-                    for (int qq = 0; qq < M; ++qq) {
-                        double2 A = Vm[qq], B = pr[qq];
-                        re += A.x * B.x - A.y * B.y;
-                        im += A.x * B.y + A.y * B.x;
-                    }
-                } else {
-                    const int D = 2 * M;
-                    const double2* Vm = v.V + vo + (int64_t)(s * M + m) * D;
-                    for (int c2 = 0; c2 < 2; ++c2) {
-                        const double2* pr = v.p + ((int64_t)(k * 2 + c2) * v.max_bands + band) * v.MT + mo;
-                        for (int qq = 0; qq < M; ++qq) {
-                            double2 A = Vm[c2 * M + qq], B = pr[qq];
-                            re += A.x * B.x - A.y * B.y;
-                            im += A.x * B.y + A.y * B.x;
-                        }
-                    }
-                }
+                const double2 w = v.cv[((int64_t)ks * v.max_bands + band) * v.MT + mo + m];   // (V p)_m
+                const double re = w.x, im = w.y;
                 double2 ph = v.seg_phase[t.seg * v.nk + k];   // exp(+ikT); the scatter uses its conjugate
                 double2 cf = *reinterpret_cast<const double2*>(a.coef);
                 double2 pc = make_double2(cf.x * ph.x + cf.y * ph.y, cf.y * ph.x - cf.x * ph.y);   // cf * conj(ph)
@@ -430,10 +410,10 @@ static cudaError_t run_apply(const View& v, ApplyArgs a, const int* color_order,
 // The shapes selectable with dftu_set_kernel_variant, listed once for the single-system and the batched
 // launches: X(variant, lanes per band Q, band groups per CTA, points in flight per lane, L2 prefetch).
 // Variant 0, and 6 and 7, take the default case of each switch.
-#define DFTU_APPLY_SHAPES_F32(X) X(1, 8, 4, 4, 0) X(2, 4, 4, 8, 0) X(3, 16, 4, 4, 0) X(4, 8, 4, 8, 1) X(5, 8, 4, 4, 1)
-#define DFTU_APPLY_DEFAULT_F32 8, 4, 8, 0
-#define DFTU_APPLY_SHAPES_PAIR(X) X(1, 8, 4, 2, 0) X(2, 4, 4, 4, 0) X(3, 8, 4, 8, 0) X(4, 8, 4, 4, 1) X(5, 4, 4, 4, 1)
-#define DFTU_APPLY_DEFAULT_PAIR 8, 4, 4, 0
+#define DFTU_APPLY_SHAPES_F32(X) X(1, 8, 4, 4, 1) X(2, 16, 4, 8, 1) X(3, 16, 4, 4, 0) X(4, 8, 4, 8, 0) X(5, 16, 4, 4, 1)
+#define DFTU_APPLY_DEFAULT_F32 8, 4, 8, 1
+#define DFTU_APPLY_SHAPES_PAIR(X) X(1, 8, 4, 4, 1) X(2, 16, 4, 2, 1) X(3, 8, 4, 8, 1) X(4, 16, 2, 4, 1) X(5, 16, 4, 4, 0)
+#define DFTU_APPLY_DEFAULT_PAIR 16, 4, 4, 1
 
 cudaError_t launch_apply(const View& v, void* psi, dftu_prec prec, dftu_f64_mode mode, int nbands,
                          int64_t sk, int64_t ss, int64_t sn, const double* coef, const int* color_order,
@@ -459,6 +439,61 @@ cudaError_t launch_apply(const View& v, void* psi, dftu_prec prec, dftu_f64_mode
     }
 #undef DFTU_CASE_F32
 #undef DFTU_CASE_PAIR
+}
+
+// cv[ks][band][moff_I + m] = sum_m' V^I_mm' p_m' (collinear: the spin block of ks; non-collinear: the
+// 2M x 2M matrix over both spinor components of the band).  The apply multiplies it by each segment's
+// conjugate Bloch phase and the caller's coefficient.
+__device__ __forceinline__ void coefvec_elem(const View& v, int nbands, int64_t g) {
+    const int64_t rows = (int64_t)v.nk * v.ns * nbands;
+    if (g >= rows * v.MT) return;
+    const int64_t rowi = g / v.MT;
+    const int j = (int)(g % v.MT);
+    const int ks = (int)(rowi / nbands), band = (int)(rowi % nbands);
+    const int a = v.orb_atom[j];
+    const int M = v.atom_M[a], mo = v.atom_moff[a], m = j - mo;
+    const int64_t vo = v.atom_mat_off[a];
+    const int k = ks / v.ns, s = ks % v.ns;
+    double re = 0.0, im = 0.0;
+    if (!v.noncollinear) {
+        const double2* Vm = v.V + vo + (int64_t)s * M * M + m * M;
+        const double2* pr = v.p + ((int64_t)ks * v.max_bands + band) * v.MT + mo;
+        for (int qq = 0; qq < M; ++qq) {
+            const double2 A = Vm[qq], B = pr[qq];
+            re += A.x * B.x - A.y * B.y;
+            im += A.x * B.y + A.y * B.x;
+        }
+    } else {
+        const int D = 2 * M;
+        const double2* Vm = v.V + vo + (int64_t)(s * M + m) * D;
+        for (int c2 = 0; c2 < 2; ++c2) {
+            const double2* pr = v.p + ((int64_t)(k * 2 + c2) * v.max_bands + band) * v.MT + mo;
+            for (int qq = 0; qq < M; ++qq) {
+                const double2 A = Vm[c2 * M + qq], B = pr[qq];
+                re += A.x * B.x - A.y * B.y;
+                im += A.x * B.y + A.y * B.x;
+            }
+        }
+    }
+    v.cv[((int64_t)ks * v.max_bands + band) * v.MT + j] = make_double2(re, im);
+}
+
+__global__ void k_coefvec(View v, int nbands) { coefvec_elem(v, nbands, (int64_t)blockIdx.x * blockDim.x + threadIdx.x); }
+
+__global__ void k_coefvec_batch(const View* __restrict__ views, const ProjArgs* __restrict__ args) {
+    coefvec_elem(views[blockIdx.y], args[blockIdx.y].nbands, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+cudaError_t launch_coefvec(const View& v, int nbands, cudaStream_t st) {
+    const int64_t n = (int64_t)v.nk * v.ns * nbands * v.MT;
+    k_coefvec<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(v, nbands);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coefvec_batch(const BatchLaunch& b, cudaStream_t st) {
+    dim3 grid((unsigned)((b.max_reduce + 255) / 256), b.nsys);
+    k_coefvec_batch<<<grid, 256, 0, st>>>(b.views, b.args);
+    return cudaGetLastError();
 }
 
 // Taylor coefficients of exp(-i dt H): term j = (-i dt / j) H term_{j-1}.

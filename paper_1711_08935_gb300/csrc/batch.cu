@@ -244,8 +244,10 @@ dftu_status dftu_batch_apply(dftu_batch b, const double* coef, int accumulate, d
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(b->device);
-    cudaError_t e = launch_apply_batch(b->L, b->prec, c0->f64_mode, c0->variant[b->prec == DFTU_C64 ? 3 : 2],
-                                       coef ? coef : c0->d_coef_one, accumulate ? 1 : 0, reinterpret_cast<cudaStream_t>(stream));
+    cudaError_t e = launch_coefvec_batch(b->L, reinterpret_cast<cudaStream_t>(stream));
+    if (e == cudaSuccess)
+        e = launch_apply_batch(b->L, b->prec, c0->f64_mode, c0->variant[b->prec == DFTU_C64 ? 3 : 2], coef ? coef : c0->d_coef_one,
+                               accumulate ? 1 : 0, reinterpret_cast<cudaStream_t>(stream));
     if (prev >= 0) cudaSetDevice(prev);
     if (e != cudaSuccess) return bfail(b, DFTU_ERR_CUDA, std::string("batch_apply: ") + cudaGetErrorString(e));
     return DFTU_OK;

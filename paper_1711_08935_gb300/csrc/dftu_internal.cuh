@@ -104,6 +104,21 @@ struct View {
     double2* V;            // same layout, U_eff (1/2 - rho)
     const double* coul;
     const int* coul_set;   // [nspecies] 1 if set
+    double2* cv;           // [nk*ns][max_bands][MT] coefficient vectors the apply scatters: V p, or the sum
+                           // of the Taylor terms' coefficients (dftu_taylor_step)
+    const int* orb_atom;   // [MT] atom of each orbital slot
+    // Overlap of the scattered orbitals with the gathered ones, by blocks of atom pairs (I, J) that share
+    // grid points, per lattice-image difference: B[m][m'] = dV sum phi_Im(a) phi_Jm'(b) over point pairs
+    // (a of I, b of J) on the same grid point.  Rows of the block list are grouped by I.
+    int nblk;
+    const int* blk_rowptr;    // [natoms + 1]
+    const int* blk_J;         // [nblk]
+    const int64_t* blk_off;   // [nblk] offset of the block's M_I x M_J values in blk_data
+    const double* blk_data;
+    const double* blk_D;      // [nblk][3] image difference (T_a - T_b) L, bohr
+    const double* blk_Dg;     // [nblk][3] the same minus (R_I - R_J): d_a - d_b of the gauge phases
+    double2* blk_phase;       // [nk][nblk] exp(+i k.D) (times exp(+i A.Dg) with a vector potential)
+    double* gaugeA;           // [3] the vector potential of the last dftu_set_vector_potential
     double* U;
     double* J;
     double* E;             // [natoms]
@@ -197,6 +212,12 @@ cudaError_t launch_apply(const View& v, void* psi, dftu_prec prec, dftu_f64_mode
                          const std::vector<int>& color_beg, int variant, int accumulate, cudaStream_t st,
                          bool gauge = false);
 cudaError_t launch_gauge_phases(const View& v, const double* A, cudaStream_t st);
+// cv = V p for the first nbands bands (the coefficients the apply scatters).
+cudaError_t launch_coefvec(const View& v, int nbands, cudaStream_t st);
+cudaError_t launch_coefvec_batch(const BatchLaunch& b, cudaStream_t st);
+// Taylor step in the span of the orbitals: cv = sum_{j=1}^{order} c_j V p_{j-1}, p_0 = p, p_j = c_j O V p_{j-1}
+// (O: the block overlap above), coefs = the order complex c_j on the device.
+cudaError_t launch_taylor_cv(const View& v, int nbands, int order, const double* coefs, bool gauge, cudaStream_t st);
 // Projections onto three orbital tables (v.phi* + a * v.phi_dir_stride, a = 0..2) in one launch, the
 // directions interleaved per tile so that the three reads of a tile's states share L2; results go to
 // p_out + a * p_stride.

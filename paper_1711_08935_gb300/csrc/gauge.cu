@@ -25,6 +25,7 @@ __device__ __forceinline__ void displacement(const View& v, int64_t j, int atom,
 
 // exp(+i A.d_j) for every sphere point: FP64 (cos, sin) and the FP32 pair split (hi, hi, lo, lo).
 __global__ void k_gauge_phases(View v, const double* __restrict__ A) {
+    if (blockIdx.x == 0 && threadIdx.x < 3) v.gaugeA[threadIdx.x] = A[threadIdx.x];   // for the real-time step
     const Tile t = v.tiles[blockIdx.x];
     const int i = threadIdx.x;
     if (i >= t.np) return;

@@ -399,9 +399,249 @@ __device__ __forceinline__ void proj_body_pair(const View& v, const Tile& t, int
 }
 
 // ------------------------------------------------------------------------------------------------
+// PAIR policy with paired orbitals (complex128 states)
+// ------------------------------------------------------------------------------------------------
+// The arithmetic of proj_body_pair (split states, offset accumulator, residual in a second float),
+// with the shared-memory rows of the F32 policy: per point [hi_0 .. hi_{MP-1}, lo_0 .. lo_{MP-1}].
+// Two orbitals share one 8-byte shared load and every f32x2 instruction, against a broadcast state
+// component, so a point costs MP/2 hi and MP/2 lo loads instead of M 16-byte (hi, hi, lo, lo) loads.
+template <int M, int Q, int CH, int PF>
+__device__ __forceinline__ void proj_body_pair2(const View& v, const Tile& t, int ks, int band, const double2* __restrict__ row,
+                                                const int* s_idx, const float* s_phf, int pe, int64_t poff) {
+    constexpr int MP = (M + 1) & ~1, NP = MP / 2;
+    const int q = threadIdx.x & (Q - 1);
+    DF2 Rr[NP], Ri[NP];   // running sums of the real and imaginary parts, orbitals (2j, 2j+1)
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        Rr[j] = DF2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        Ri[j] = Rr[j];
+    }
+    int Em_run = 0;
+    bool bad = false;
+    constexpr int LOG2CH = (CH >= 16) ? 4 : (CH >= 8) ? 3 : (CH >= 4) ? 2 : (CH >= 2) ? 1 : 0;
+    const float Cv = pow2f(min(max(pe + 3 + LOG2CH, -100), 100));   // >= 4 * CH * max|phi x'|, |x'| < 2
+    const float2 C2 = make_float2(Cv, Cv);
+    const float2 mone = make_float2(-1.f, -1.f);
+    if (row) {
+        for (int i0 = q; i0 < t.np; i0 += Q * CH) {
+            double2 x[CH];
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                int i = i0 + c * Q;
+                x[c] = (i < t.np) ? __ldg(row + s_idx[i]) : make_double2(0.0, 0.0);
+            }
+            if (PF) {
+#pragma unroll
+                for (int c = 0; c < CH; ++c) {
+                    int i = i0 + Q * CH + c * Q;
+                    if (i < t.np) prefetch_l2(row + s_idx[i]);
+                }
+            }
+            int Ec = 0;
+#pragma unroll
+            for (int c = 0; c < CH; ++c) Ec = max(Ec, max(exp_field(x[c].x), exp_field(x[c].y)));
+            if (Ec == 0x7FF) bad = true;
+            if (Ec == 0) continue;
+            Ec = max(Ec, 127);
+            if (Ec > Em_run) {
+                if (Em_run != 0) {
+                    const float sc = pow2f(Em_run - Ec);
+                    const float2 s2 = make_float2(sc, sc);
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) {
+                        Rr[j].h = __fmul2_rn(Rr[j].h, s2); Rr[j].l = __fmul2_rn(Rr[j].l, s2);
+                        Ri[j].h = __fmul2_rn(Ri[j].h, s2); Ri[j].l = __fmul2_rn(Ri[j].l, s2);
+                    }
+                }
+                Em_run = Ec;
+            }
+            float2 aR[NP], lR[NP], aI[NP], lI[NP];
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                aR[j] = C2; aI[j] = C2;
+                lR[j] = make_float2(0.f, 0.f); lI[j] = lR[j];
+            }
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                float rh, rl, ih, il;
+                split_scaled(x[c].x, Em_run, rh, rl);
+                split_scaled(x[c].y, Em_run, ih, il);
+                const float2 brh = make_float2(rh, rh), brl = make_float2(rl, rl);
+                const float2 bih = make_float2(ih, ih), bil = make_float2(il, il);
+                const float* ph = s_phf + (i0 + c * Q) * (2 * MP);
+#pragma unroll
+                for (int j = 0; j < NP; ++j) {
+                    const float2 ah = *reinterpret_cast<const float2*>(ph + 2 * j);
+                    const float2 al = *reinterpret_cast<const float2*>(ph + MP + 2 * j);
+                    float2 sr = ffma2(ah, brh, aR[j]);
+                    float2 tr = ffma2(sr, mone, aR[j]);                // aR - sr, exact
+                    lR[j] = fadd2(lR[j], ffma2(ah, brh, tr));           // rounding residual
+                    lR[j] = ffma2(ah, brl, lR[j]);
+                    lR[j] = ffma2(al, brh, lR[j]);
+                    aR[j] = sr;
+                    float2 si = ffma2(ah, bih, aI[j]);
+                    float2 ti = ffma2(si, mone, aI[j]);
+                    lI[j] = fadd2(lI[j], ffma2(ah, bih, ti));
+                    lI[j] = ffma2(ah, bil, lI[j]);
+                    lI[j] = ffma2(al, bih, lI[j]);
+                    aI[j] = si;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                df_add(Rr[j], DF2{fadd2(aR[j], make_float2(-Cv, -Cv)), lR[j]});
+                df_add(Ri[j], DF2{fadd2(aI[j], make_float2(-Cv, -Cv)), lI[j]});
+            }
+        }
+    }
+    int Em_max = Em_run;
+#pragma unroll
+    for (int off = Q / 2; off > 0; off >>= 1) Em_max = max(Em_max, __shfl_xor_sync(0xffffffffu, Em_max, off));
+    if (Em_run != Em_max) {
+        const float sc = (Em_run == 0) ? 0.0f : pow2f(Em_run - Em_max);
+        const float2 s2 = make_float2(sc, sc);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            Rr[j].h = __fmul2_rn(Rr[j].h, s2); Rr[j].l = __fmul2_rn(Rr[j].l, s2);
+            Ri[j].h = __fmul2_rn(Ri[j].h, s2); Ri[j].l = __fmul2_rn(Ri[j].l, s2);
+        }
+    }
+#pragma unroll
+    for (int off = Q / 2; off > 0; off >>= 1)
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            DF2 o{make_float2(shfl_x(Rr[j].h.x, off), shfl_x(Rr[j].h.y, off)),
+                  make_float2(shfl_x(Rr[j].l.x, off), shfl_x(Rr[j].l.y, off))};
+            df_add(Rr[j], o);
+            DF2 u{make_float2(shfl_x(Ri[j].h.x, off), shfl_x(Ri[j].h.y, off)),
+                  make_float2(shfl_x(Ri[j].l.x, off), shfl_x(Ri[j].l.y, off))};
+            df_add(Ri[j], u);
+        }
+    int anybad = bad ? 1 : 0;
+#pragma unroll
+    for (int off = Q / 2; off > 0; off >>= 1) anybad |= __shfl_xor_sync(0xffffffffu, anybad, off);
+    if (row) {
+        const int sc = Em_max - 1023;
+        per_lane_orbital<M, Q>(q, [&](int mq) {
+            float rh = Rr[0].h.x, rl = Rr[0].l.x, ih = Ri[0].h.x, il = Ri[0].l.x;
+#pragma unroll
+            for (int m = 1; m < M; ++m)
+                if (m == mq) {
+                    const DF2& a = Rr[m / 2];
+                    const DF2& b = Ri[m / 2];
+                    rh = (m & 1) ? a.h.y : a.h.x;
+                    rl = (m & 1) ? a.l.y : a.l.x;
+                    ih = (m & 1) ? b.h.y : b.h.x;
+                    il = (m & 1) ? b.l.y : b.l.x;
+                }
+            double re = f2d_scaled(rh, sc) + f2d_scaled(rl, sc);
+            double im = f2d_scaled(ih, sc) + f2d_scaled(il, sc);
+            if (anybad) { re = __longlong_as_double(0x7FF8000000000000LL); im = re; }
+            write_partial(v, t, ks, band, mq, re, im, poff);
+        });
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// F32 policy, two bands per lane (complex64 states)
+// ------------------------------------------------------------------------------------------------
+// Every lane walks its points for two bands at once, so each grid index and each paired orbital load
+// from shared memory serves both.  Products are compensated as in proj_body_f32 (phi = hi + lo, both
+// halves multiplied by the FP32 state value); the sums are plain FP32 over the lane's points of the
+// tile, then over the Q lanes, and FP64 from there on (across tiles).
+template <int M, int Q, int CH, int PF>
+__device__ __forceinline__ void proj_body_f32x2(const View& v, const Tile& t, int ks, int band, int nbands,
+                                                const float2* __restrict__ row0, const float2* __restrict__ row1,
+                                                const int* s_idx, const float* s_phf, int64_t poff) {
+    constexpr int MP = (M + 1) & ~1, NP = MP / 2;
+    const int q = threadIdx.x & (Q - 1);
+    // [band][part]: real hi, imaginary hi, real lo, imaginary lo of orbitals (2j, 2j+1)
+    float2 S0[4][NP], S1[4][NP];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int j = 0; j < NP; ++j) { S0[a][j] = make_float2(0.f, 0.f); S1[a][j] = S0[a][j]; }
+    if (row0) {
+        for (int i0 = q; i0 < t.np; i0 += Q * CH) {
+            float2 x0[CH], x1[CH];
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int i = i0 + c * Q;
+                const bool in = i < t.np;
+                const int g = in ? s_idx[i] : 0;
+                x0[c] = in ? __ldg(row0 + g) : make_float2(0.f, 0.f);
+                x1[c] = (in && row1) ? __ldg(row1 + g) : make_float2(0.f, 0.f);
+            }
+            if (PF) {
+#pragma unroll
+                for (int c = 0; c < CH; ++c) {
+                    const int i = i0 + Q * CH + c * Q;
+                    if (i < t.np) {
+                        prefetch_l2(row0 + s_idx[i]);
+                        if (row1) prefetch_l2(row1 + s_idx[i]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const float* ph = s_phf + (i0 + c * Q) * (2 * MP);
+                const float2 r0 = make_float2(x0[c].x, x0[c].x), m0 = make_float2(x0[c].y, x0[c].y);
+                const float2 r1 = make_float2(x1[c].x, x1[c].x), m1 = make_float2(x1[c].y, x1[c].y);
+#pragma unroll
+                for (int j = 0; j < NP; ++j) {
+                    const float2 h2 = *reinterpret_cast<const float2*>(ph + 2 * j);
+                    const float2 l2 = *reinterpret_cast<const float2*>(ph + MP + 2 * j);
+                    S0[0][j] = ffma2(h2, r0, S0[0][j]); S0[1][j] = ffma2(h2, m0, S0[1][j]);
+                    S0[2][j] = ffma2(l2, r0, S0[2][j]); S0[3][j] = ffma2(l2, m0, S0[3][j]);
+                    S1[0][j] = ffma2(h2, r1, S1[0][j]); S1[1][j] = ffma2(h2, m1, S1[1][j]);
+                    S1[2][j] = ffma2(l2, r1, S1[2][j]); S1[3][j] = ffma2(l2, m1, S1[3][j]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int off = Q / 2; off > 0; off >>= 1)
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                S0[a][j] = fadd2(S0[a][j], make_float2(shfl_x(S0[a][j].x, off), shfl_x(S0[a][j].y, off)));
+                S1[a][j] = fadd2(S1[a][j], make_float2(shfl_x(S1[a][j].x, off), shfl_x(S1[a][j].y, off)));
+            }
+    if (row0) {
+        per_lane_orbital<M, Q>(q, [&](int mq) {
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                if (b == 1 && !row1) break;
+                float v4[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const float2 w = (b == 0) ? S0[a][0] : S1[a][0];
+                    v4[a] = w.x;
+                }
+#pragma unroll
+                for (int m = 1; m < M; ++m)
+                    if (m == mq)
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) {
+                            const float2 w = (b == 0) ? S0[a][m / 2] : S1[a][m / 2];
+                            v4[a] = (m & 1) ? w.y : w.x;
+                        }
+                write_partial(v, t, ks, band + b, mq, f2d_scaled(v4[0], 0) + f2d_scaled(v4[2], 0),
+                              f2d_scaled(v4[1], 0) + f2d_scaled(v4[3], 0), poff);
+            }
+        });
+    }
+    (void)nbands;
+}
+
+// ------------------------------------------------------------------------------------------------
 // kernels
 // ------------------------------------------------------------------------------------------------
-enum Pol { P_F64 = 0, P_PAIR = 1, P_F32 = 2 };
+enum Pol { P_F64 = 0, P_PAIR = 1, P_F32 = 2, P_PAIR2 = 3, P_F32B2 = 4 };
+
+// bands a lane carries at once
+template <int POL> struct LaneBands { static constexpr int value = (POL == P_F32B2) ? 2 : 1; };
 
 // One work item: tile `tile_id` of the system described by (v, a), spin/component index ks, every band of
 // band chunk `chunk` (NBG groups of BPC bands), against orbital table `dir` (0 unless the launch projects
@@ -414,7 +654,8 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
     const int64_t ph0 = t.phi0 + dir * v.phi_dir_stride;   // this table's rows of the tile
     const int64_t poff = dir * v.part_dir_stride;
     const int k = ks / v.ns, s = ks % v.ns;
-    constexpr int BPW = 32 / Q;
+    constexpr int NBL = LaneBands<POL>::value;   // bands per lane
+    constexpr int BPW = (32 / Q) * NBL;
     constexpr int BPC = (CTA / 32) * BPW;
 
     // ---- stage the tile once (grid indices, orbital rows, orbital exponent bound)
@@ -425,16 +666,19 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
         double* s_phi = reinterpret_cast<double*>(smem + TILE * sizeof(int));
         for (int e = threadIdx.x; e < TILE * t.M; e += CTA)
             s_phi[e] = (e < t.np * t.M) ? v.phi64[ph0 + e] : 0.0;
-    } else if (POL == P_F32) {
+    } else if (POL == P_F32 || POL == P_PAIR2 || POL == P_F32B2) {
         float* s_phf = reinterpret_cast<float*>(smem + TILE * sizeof(int));
         const int MP = (t.M + 1) & ~1;
+        int pe = -200;
         for (int e = threadIdx.x; e < TILE_PAD * MP; e += CTA) {
             const int i = e / MP, m = e - i * MP;
             float hi = 0.f, lo = 0.f;
             if (i < t.np && m < t.M) { hi = v.phi_hi[ph0 + (int64_t)i * t.M + m]; lo = v.phi_lo[ph0 + (int64_t)i * t.M + m]; }
             s_phf[i * 2 * MP + m] = hi;
             s_phf[i * 2 * MP + MP + m] = lo;
+            if (hi != 0.f) pe = max(pe, ((__float_as_int(hi) >> 23) & 0xFF) - 127 + 1);   // |hi| < 2^pe
         }
+        if (POL == P_PAIR2) atomicMax(s_pe, pe);
     } else {
         float4* s_phi = reinterpret_cast<float4*>(smem + TILE * sizeof(int));
         int pe = -200;
@@ -462,10 +706,30 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
     for (int g = 0; g < NBG; ++g) {
         const int band0 = (chunk * NBG + g) * BPC;
         if (band0 >= a.nbands) break;
-        const int band = band0 + (threadIdx.x >> 5) * BPW + ((threadIdx.x & 31) / Q);
+        const int band = band0 + (threadIdx.x >> 5) * BPW + ((threadIdx.x & 31) / Q) * NBL;
         const bool active = band < a.nbands;
         const int64_t off = (int64_t)k * a.sk + (int64_t)s * a.ss + (int64_t)band * a.sn;
-        if (POL == P_F64) {
+        if (POL == P_PAIR2) {
+            const float* s_phf = reinterpret_cast<const float*>(smem + TILE * sizeof(int));
+            const double2* row = active ? reinterpret_cast<const double2*>(a.psi) + off : nullptr;
+            const int pe = *s_pe;
+            switch (t.M) {
+                case 1: proj_body_pair2<1, Q, CH, PF>(v, t, ks, band, row, s_idx, s_phf, pe, poff); break;
+                case 3: proj_body_pair2<3, Q, CH, PF>(v, t, ks, band, row, s_idx, s_phf, pe, poff); break;
+                case 5: proj_body_pair2<5, Q, CH, PF>(v, t, ks, band, row, s_idx, s_phf, pe, poff); break;
+                default: proj_body_pair2<7, Q, CH, PF>(v, t, ks, band, row, s_idx, s_phf, pe, poff); break;
+            }
+        } else if (POL == P_F32B2) {
+            const float* s_phf = reinterpret_cast<const float*>(smem + TILE * sizeof(int));
+            const float2* row0 = active ? reinterpret_cast<const float2*>(a.psi) + off : nullptr;
+            const float2* row1 = (band + 1 < a.nbands) ? row0 + a.sn : nullptr;
+            switch (t.M) {
+                case 1: proj_body_f32x2<1, Q, CH, PF>(v, t, ks, band, a.nbands, row0, row1, s_idx, s_phf, poff); break;
+                case 3: proj_body_f32x2<3, Q, CH, PF>(v, t, ks, band, a.nbands, row0, row1, s_idx, s_phf, poff); break;
+                case 5: proj_body_f32x2<5, Q, CH, PF>(v, t, ks, band, a.nbands, row0, row1, s_idx, s_phf, poff); break;
+                default: proj_body_f32x2<7, Q, CH, PF>(v, t, ks, band, a.nbands, row0, row1, s_idx, s_phf, poff); break;
+            }
+        } else if (POL == P_F64) {
             const double* s_phi = reinterpret_cast<const double*>(smem + TILE * sizeof(int));
             const double2* row = active ? reinterpret_cast<const double2*>(a.psi) + off : nullptr;
             const double2* s_g = reinterpret_cast<const double2*>(s_gauge);
@@ -518,7 +782,7 @@ __global__ void __launch_bounds__(CTA, MINB) k_project_batch(const View* __restr
                                                           const int4* __restrict__ items, int nitems, int* counter) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_pe, s_item;
-    constexpr int BPC = (CTA / 32) * (32 / Q);
+    constexpr int BPC = (CTA / 32) * (32 / Q) * LaneBands<POL>::value;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
         __syncthreads();
@@ -610,30 +874,31 @@ static cudaError_t run_project(const View& v, const ProjArgs& a, cudaStream_t st
     cudaError_t e = cudaSuccess;
     if (!smem_configured((const void*)fn, (int)smem)) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    constexpr int BPC = (CTA / 32) * (32 / Q);
+    constexpr int BPC = (CTA / 32) * (32 / Q) * LaneBands<POL>::value;
     dim3 grid(v.ntiles * NDIR, (a.nbands + BPC * NBG - 1) / (BPC * NBG), v.nk * v.ns);
     fn<<<grid, CTA, smem, st>>>(v, a);
     return cudaGetLastError();
 }
 
 // The shapes selectable with dftu_set_kernel_variant, listed once for the single-system and the batched
-// launches: X(variant, lanes per band Q, points per chain, band groups per CTA, L2 prefetch, minimum
-// blocks per SM).  Variant 0 is the default case of each switch.
+// launches: X(variant, policy, lanes per band Q, points per chain, band groups per CTA, L2 prefetch,
+// minimum blocks per SM).  Variant 0 is the default case of each switch.  P_PAIR2 is the FP32-pair
+// arithmetic with paired orbitals, P_F32B2 the complex64 form with two bands per lane.
 #define DFTU_PROJECT_SHAPES_F32(X) \
-    X(1, 8, 8, 4, 0, 2) X(2, 16, 8, 4, 0, 2) X(3, 4, 16, 4, 0, 2) X(4, 8, 16, 4, 1, 2) \
-    X(5, 8, 16, 8, 0, 2) X(6, 8, 8, 4, 0, 3) X(7, 8, 16, 2, 0, 2)
-#define DFTU_PROJECT_DEFAULT_F32 8, 16, 4, 0, 2
+    X(1, P_F32, 8, 16, 8, 0, 2) X(2, P_F32B2, 8, 8, 2, 0, 2) X(3, P_F32B2, 8, 8, 8, 0, 2) X(4, P_F32B2, 4, 16, 2, 0, 2) \
+    X(5, P_F32B2, 16, 8, 4, 0, 2) X(6, P_F32B2, 8, 12, 4, 0, 2) X(7, P_F32B2, 8, 8, 4, 0, 3)
+#define DFTU_PROJECT_DEFAULT_F32 P_F32B2, 8, 8, 4, 0, 2
 #define DFTU_PROJECT_SHAPES_PAIR(X) \
-    X(1, 4, 8, 8, 1, 2) X(2, 4, 8, 4, 0, 2) X(3, 4, 8, 2, 1, 2) X(4, 4, 8, 4, 1, 2) \
-    X(5, 8, 8, 4, 1, 2) X(6, 4, 4, 4, 0, 3) X(7, 4, 8, 4, 1, 3)
-#define DFTU_PROJECT_DEFAULT_PAIR 8, 8, 4, 0, 2
+    X(1, P_PAIR, 4, 8, 4, 1, 2) X(2, P_PAIR, 4, 8, 4, 0, 2) X(3, P_PAIR2, 4, 8, 8, 1, 2) X(4, P_PAIR, 4, 16, 4, 1, 2) \
+    X(5, P_PAIR, 8, 8, 4, 1, 2) X(6, P_PAIR, 4, 4, 8, 1, 2) X(7, P_PAIR, 8, 16, 4, 1, 2)
+#define DFTU_PROJECT_DEFAULT_PAIR P_PAIR, 4, 8, 8, 1, 2
 
 cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_f64_mode mode, int nbands,
                            int64_t sk, int64_t ss, int64_t sn, int variant, cudaStream_t st, bool gauge) {
     ProjArgs a{psi, sk, ss, sn, nbands};
     cudaError_t e;
-#define DFTU_CASE_F32(i, Q, CH, NBG, PF, MB) case i: e = run_project<P_F32, Q, CH, NBG, PF, MB>(v, a, st); break;
-#define DFTU_CASE_PAIR(i, Q, CH, NBG, PF, MB) case i: e = run_project<P_PAIR, Q, CH, NBG, PF, MB>(v, a, st); break;
+#define DFTU_CASE_F32(i, POL, Q, CH, NBG, PF, MB) case i: e = run_project<POL, Q, CH, NBG, PF, MB>(v, a, st); break;
+#define DFTU_CASE_PAIR(i, POL, Q, CH, NBG, PF, MB) case i: e = run_project<POL, Q, CH, NBG, PF, MB>(v, a, st); break;
     if (gauge) {   // one shape per arithmetic policy with the gauge phases (Sec. V)
         if (prec == DFTU_C64) e = run_project<P_F32, 8, 16, 8, 0, 2, 1>(v, a, st);
         else if (mode == DFTU_F64_NATIVE) e = run_project<P_F64, 8, 1, 4, 0, 2, 1>(v, a, st);
@@ -641,14 +906,14 @@ cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_
     } else if (prec == DFTU_C64) {
         switch (variant) {
             DFTU_PROJECT_SHAPES_F32(DFTU_CASE_F32)
-            default: e = run_project<P_F32, DFTU_PROJECT_DEFAULT_F32>(v, a, st); break;
+            default: e = run_project<DFTU_PROJECT_DEFAULT_F32>(v, a, st); break;
         }
     } else if (mode == DFTU_F64_NATIVE) {
         e = run_project<P_F64, 8, 1, 4, 0>(v, a, st);
     } else {
         switch (variant) {
             DFTU_PROJECT_SHAPES_PAIR(DFTU_CASE_PAIR)
-            default: e = run_project<P_PAIR, DFTU_PROJECT_DEFAULT_PAIR>(v, a, st); break;
+            default: e = run_project<DFTU_PROJECT_DEFAULT_PAIR>(v, a, st); break;
         }
     }
 #undef DFTU_CASE_F32
@@ -702,19 +967,19 @@ static cudaError_t run_project_batch(const BatchLaunch& b, cudaStream_t st) {
 
 cudaError_t launch_project_batch(const BatchLaunch& b, dftu_prec prec, dftu_f64_mode mode, int variant, cudaStream_t st) {
     cudaError_t e;
-#define DFTU_CASE_F32(i, Q, CH, NBG, PF, MB) case i: e = run_project_batch<P_F32, Q, CH, NBG, PF, MB>(b, st); break;
-#define DFTU_CASE_PAIR(i, Q, CH, NBG, PF, MB) case i: e = run_project_batch<P_PAIR, Q, CH, NBG, PF, MB>(b, st); break;
+#define DFTU_CASE_F32(i, POL, Q, CH, NBG, PF, MB) case i: e = run_project_batch<POL, Q, CH, NBG, PF, MB>(b, st); break;
+#define DFTU_CASE_PAIR(i, POL, Q, CH, NBG, PF, MB) case i: e = run_project_batch<POL, Q, CH, NBG, PF, MB>(b, st); break;
     if (prec == DFTU_C64) {
         switch (variant) {
             DFTU_PROJECT_SHAPES_F32(DFTU_CASE_F32)
-            default: e = run_project_batch<P_F32, DFTU_PROJECT_DEFAULT_F32>(b, st); break;
+            default: e = run_project_batch<DFTU_PROJECT_DEFAULT_F32>(b, st); break;
         }
     } else if (mode == DFTU_F64_NATIVE) {
         e = run_project_batch<P_F64, 8, 1, 4, 0>(b, st);
     } else {
         switch (variant) {
             DFTU_PROJECT_SHAPES_PAIR(DFTU_CASE_PAIR)
-            default: e = run_project_batch<P_PAIR, DFTU_PROJECT_DEFAULT_PAIR>(b, st); break;
+            default: e = run_project_batch<DFTU_PROJECT_DEFAULT_PAIR>(b, st); break;
         }
     }
 #undef DFTU_CASE_F32

@@ -34,7 +34,8 @@ EXPORTED = ["dftu_create", "dftu_setup_atoms", "dftu_get_sphere", "dftu_coulomb_
             "dftu_taylor_step", "dftu_batch_create", "dftu_batch_bind", "dftu_batch_project",
             "dftu_batch_occupations", "dftu_batch_acbn0_uj", "dftu_batch_apply", "dftu_batch_last_error",
             "dftu_batch_destroy", "dftu_forces", "dftu_radius_cell", "dftu_radius_threshold",
-            "dftu_set_vector_potential", "dftu_hubbard_current", "dftu_fll_energy"]
+            "dftu_set_vector_potential", "dftu_hubbard_current", "dftu_fll_energy", "dftu_occupation_elems",
+            "dftu_export_occupations", "dftu_import_occupations"]
 
 
 class DftuGrid(C.Structure):
@@ -105,12 +106,16 @@ def load() -> C.CDLL:
         "dftu_set_kernel_variant": [vp, i32, i32],
         "dftu_kernel_variants": [i32],
         "dftu_project_sphere_noalloc": [vp, i32, i32, i64, vp, vp, vp, i32, i32, d, vp, vp],
+        "dftu_occupation_elems": [vp],
+        "dftu_export_occupations": [vp, vp, vp],
+        "dftu_import_occupations": [vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
         fn.argtypes = args
         fn.restype = C.c_int
     L.dftu_last_error.restype = C.c_char_p
+    L.dftu_occupation_elems.restype = C.c_int64
     L.dftu_destroy.restype = None
     L.dftu_batch_last_error.restype = C.c_char_p
     L.dftu_radius_cell.restype = C.c_double
@@ -256,6 +261,24 @@ class Handle:
     def occupations(self, f: torch.Tensor, stream=None):
         self._check(self.lib.dftu_occupations(self.h, self._f_arg(f), _stream_ptr(stream, self.device)))
 
+    def occupation_sums(self, out: torch.Tensor = None, stream=None) -> torch.Tensor:
+        """This handle's occupation sums (rho, Pbar) of the last occupations, as a float64 tensor on the
+        handle's device (written into `out` when given) -- the part a rank adds up with the others."""
+        n = int(self.lib.dftu_occupation_elems(self.h))
+        if out is None:
+            out = torch.empty(n, dtype=torch.float64, device=torch.device("cuda", self.device))
+        if out.dtype != torch.float64 or out.numel() != n or not out.is_contiguous():
+            raise ValueError(f"out must be a contiguous float64 tensor of {n} elements")
+        self._check(self.lib.dftu_export_occupations(self.h, C.c_void_p(out.data_ptr()), _stream_ptr(stream, self.device)))
+        return out
+
+    def set_occupation_sums(self, sums: torch.Tensor, stream=None):
+        """Overwrite the occupation sums (e.g. with their total over ranks) before acbn0_uj."""
+        n = int(self.lib.dftu_occupation_elems(self.h))
+        if sums.dtype != torch.float64 or sums.numel() != n or not sums.is_contiguous():
+            raise ValueError(f"sums must be a contiguous float64 tensor of {n} elements")
+        self._check(self.lib.dftu_import_occupations(self.h, C.c_void_p(sums.data_ptr()), _stream_ptr(stream, self.device)))
+
     def acbn0_uj(self, stream=None):
         self._check(self.lib.dftu_acbn0_uj(self.h, _stream_ptr(stream, self.device)))
 
@@ -306,11 +329,14 @@ class Handle:
         self._check(self.lib.dftu_fll_energy(self.h, _dp(ee), _dp(dc), _stream_ptr(stream, self.device)))
         return ee, dc
 
-    def taylor_step(self, psi: torch.Tensor, work: torch.Tensor, f: torch.Tensor, dt: float, order: int = 4, stream=None):
+    def taylor_step(self, psi: torch.Tensor, work: Optional[torch.Tensor], f: torch.Tensor, dt: float, order: int = 4,
+                    stream=None):
+        """One real-time step (dftu_taylor_step); `work` is not needed and may be None."""
         prec, nb, ld = self._psi_args(psi)
-        if work.shape != psi.shape or work.dtype != psi.dtype or not work.is_contiguous():
+        if work is not None and (work.shape != psi.shape or work.dtype != psi.dtype or not work.is_contiguous()):
             raise ValueError("work must match psi")
-        self._check(self.lib.dftu_taylor_step(self.h, C.c_void_p(psi.data_ptr()), C.c_void_p(work.data_ptr()), prec, nb, ld,
+        wp = C.c_void_p(work.data_ptr()) if work is not None else None
+        self._check(self.lib.dftu_taylor_step(self.h, C.c_void_p(psi.data_ptr()), wp, prec, nb, ld,
                                               self._f_arg(f), float(dt), int(order), _stream_ptr(stream, self.device)))
 
     # ------------------------------------------------------------------ results
@@ -402,6 +428,24 @@ class Batch:
 
     def occupations(self, stream=None):
         self._check(self.lib.dftu_batch_occupations(self.b, _stream_ptr(stream, self.device)))
+
+    def occupation_sums(self, out: torch.Tensor = None, stream=None) -> torch.Tensor:
+        """This handle's occupation sums (rho, Pbar) of the last occupations, as a float64 tensor on the
+        handle's device (written into `out` when given) -- the part a rank adds up with the others."""
+        n = int(self.lib.dftu_occupation_elems(self.h))
+        if out is None:
+            out = torch.empty(n, dtype=torch.float64, device=torch.device("cuda", self.device))
+        if out.dtype != torch.float64 or out.numel() != n or not out.is_contiguous():
+            raise ValueError(f"out must be a contiguous float64 tensor of {n} elements")
+        self._check(self.lib.dftu_export_occupations(self.h, C.c_void_p(out.data_ptr()), _stream_ptr(stream, self.device)))
+        return out
+
+    def set_occupation_sums(self, sums: torch.Tensor, stream=None):
+        """Overwrite the occupation sums (e.g. with their total over ranks) before acbn0_uj."""
+        n = int(self.lib.dftu_occupation_elems(self.h))
+        if sums.dtype != torch.float64 or sums.numel() != n or not sums.is_contiguous():
+            raise ValueError(f"sums must be a contiguous float64 tensor of {n} elements")
+        self._check(self.lib.dftu_import_occupations(self.h, C.c_void_p(sums.data_ptr()), _stream_ptr(stream, self.device)))
 
     def acbn0_uj(self, stream=None):
         self._check(self.lib.dftu_batch_acbn0_uj(self.b, _stream_ptr(stream, self.device)))

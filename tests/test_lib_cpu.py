@@ -20,7 +20,7 @@ def lib():
 def test_header_declarations_are_exported(lib):
     from paper_1711_08935_gb300 import dftu
     hdr = open(os.path.join(ROOT, "include", "dftu.h")).read()
-    declared = set(re.findall(r"^\s*(?:dftu_status|int|void|double|const char\*)\s+(dftu_\w+)\s*\(", hdr, re.M))
+    declared = set(re.findall(r"^\s*(?:dftu_status|int64_t|int|void|double|const char\*)\s+(dftu_\w+)\s*\(", hdr, re.M))
     assert declared == set(dftu.EXPORTED)
     out = subprocess.run(["nm", "-D", "--defined-only", dftu.LIB_PATH], capture_output=True, text=True).stdout
     exported = {l.split()[-1] for l in out.splitlines() if l.split() and l.split()[-1].startswith("dftu_")}
