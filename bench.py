@@ -329,6 +329,19 @@ def run_ours(args):
     clocks.start()
     ms64, proj64, small64, app64 = timed(psi, hpsi, args.steps, args.warmup, sampler=clocks)
     clk = clocks.stop()
+    # the access pattern's own ceiling on these buffers: gather (projection) and read-modify-write (apply)
+    def ceiling_ms(x, rmw, reps=5):
+        for _ in range(2):
+            h.access_ceiling(x, rmw)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for e0, e1 in evs:
+            e0.record(stream)
+            h.access_ceiling(x, rmw)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return statistics.median(e0.elapsed_time(e1) for e0, e1 in evs)
+
+    ceil = {"c128_gather_ms": ceiling_ms(psi, False), "c128_rmw_ms": ceiling_ms(hpsi, True)}
     # the same pass with plain FP64 fused multiply-adds (DFTU_F64_NATIVE), same states and buffers
     msn = projn = appn = None
     if not args.no_extra:
@@ -339,6 +352,8 @@ def run_ours(args):
     torch.cuda.empty_cache()
     hpsi32 = torch.zeros_like(psi32)
     ms32, proj32, small32, app32 = timed(psi32, hpsi32, args.steps, args.warmup)
+    ceil["c64_gather_ms"] = ceiling_ms(psi32, False)
+    ceil["c64_rmw_ms"] = ceiling_ms(hpsi32, True)
     del hpsi32
     status = h.sync_status()
 
@@ -396,6 +411,18 @@ def run_ours(args):
                        "differences_against": "the complex128 pass on the same states (itself held to 1e-12 of the "
                                               "oracle at full size by the GPU tests)",
                        "project_ms": round(proj32, 4), "apply_ms": round(app32, 4)},
+        "access_ceiling": {
+            "what": "one pass of the access pattern alone (dftu_access_ceiling): every sphere point read once, or read "
+                    "and written back unchanged, same tiles, no arithmetic",
+            "c128_gather_GBps": round((pb64 - orb_bytes) / (ceil["c128_gather_ms"] * 1e-3) / 1e9, 1),
+            "c128_rmw_GBps": round((ab64 - orb_bytes) / (ceil["c128_rmw_ms"] * 1e-3) / 1e9, 1),
+            "c64_gather_GBps": round((pb32 - orb_bytes) / (ceil["c64_gather_ms"] * 1e-3) / 1e9, 1),
+            "c64_rmw_GBps": round((ab32 - orb_bytes) / (ceil["c64_rmw_ms"] * 1e-3) / 1e9, 1),
+            "project_frac_of_ceiling": round(ceil["c128_gather_ms"] / proj64, 4),
+            "apply_frac_of_ceiling": round(ceil["c128_rmw_ms"] / app64, 4),
+            "pass_frac_of_ceiling": round((ceil["c128_gather_ms"] + ceil["c128_rmw_ms"]) / ms64, 4),
+            "c64_project_frac_of_ceiling": round(ceil["c64_gather_ms"] / proj32, 4),
+            "c64_apply_frac_of_ceiling": round(ceil["c64_rmw_ms"] / app32, 4)},
         "f64_native": ({"ms_per_step": round(msn, 4), "GBps": round(step_bytes64 / (msn * 1e-3) / 1e9, 2),
                         "project_ms": round(projn, 4), "apply_ms": round(appn, 4),
                         "note": "plain FP64 FMAs on this GPU's FP64 pipe (DFTU_F64_NATIVE), same states"}
@@ -408,7 +435,7 @@ def run_ours(args):
     # our kernel launches in the timed FP64 region: project (2), occupations (2), acbn0 (1), apply (coefficient
     # vectors + 1 per colour; the oxide spheres do not overlap, so one colour)
     line["gpu_launches"] = (2 + 2 + 1 + 2) * args.steps
-    if not args.no_cpu_baseline and rank == 0:
+    if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(args, s)
     if ws == 1 and not args.no_extra:
         # the other workloads of the method, each timed on the device with its own clock record

@@ -57,7 +57,7 @@ typedef enum {
     DFTU_ERR_INVALID_ARG = 1,  /* bad argument; nothing was launched */
     DFTU_ERR_NOT_READY = 2,    /* a prerequisite call is missing (setup, Coulomb, project, ...) */
     DFTU_ERR_ALLOC = 3,        /* device or host allocation failed */
-    DFTU_ERR_CUDA = 4,         /* a CUDA runtime or cuFFT call failed */
+    DFTU_ERR_CUDA = 4,         /* a CUDA runtime call or a kernel launch failed */
     DFTU_ERR_NONFINITE = 5,    /* a projection was NaN or infinite (device status) */
     DFTU_ERR_ZERO_DENOM = 6,   /* an ACBN0 denominator was < 1e-14: U = J = 0 for that atom (warning) */
     DFTU_ERR_TIMEOUT = 7       /* a bounded device-side wait gave up (device status) */
@@ -265,6 +265,14 @@ dftu_status dftu_forces(dftu_handle h, const void* const* dpsi, dftu_prec prec, 
 dftu_status dftu_project_sphere_noalloc(const void* psi, dftu_prec prec, int nbands, int64_t ld_band,
                                         const int32_t* idx, const double* phase, const double* phi, int npts,
                                         int M, double dV, double* p_out, dftu_stream stream);
+
+/* The memory-system ceiling of the access pattern, for roofline comparisons: one pass that reads every
+ * sphere point of the first nbands states once (rmw = 0, the gather of dftu_project) or reads and writes
+ * each back unchanged (rmw = 1, the read-modify-write of dftu_apply), with the same tiles and no
+ * arithmetic.  The states' values are not changed.  Not part of the method (the paper has no counterpart);
+ * the time of one pass bounds the projection and the apply on this GPU.  Asynchronous on stream. */
+dftu_status dftu_access_ceiling(dftu_handle h, void* psi, dftu_prec prec, int nbands, int64_t ld_band, int rmw,
+                                dftu_stream stream);
 
 /* ---- Several GPUs: occupation sums over disjoint parts of the (k, band) set -----------------------
  * Eq. (4) and Eq. (8) are sums over k-points and bands of w_k f |p><p| (Pbar with the per-band factor Nbar

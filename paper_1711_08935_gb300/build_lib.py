@@ -27,15 +27,6 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def _cuda_lib_dir(nvcc: str) -> str:
-    root = os.path.dirname(os.path.dirname(os.path.realpath(nvcc)))
-    for d in ("lib64", "lib", os.path.join("targets", "sbsa-linux", "lib"), os.path.join("targets", "x86_64-linux", "lib")):
-        p = os.path.join(root, d)
-        if os.path.exists(os.path.join(p, "libcufft.so")):
-            return p
-    return os.path.join(root, "lib64")
-
-
 def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
@@ -63,9 +54,8 @@ def build(verbose: bool = False) -> str:
                 sys.stderr.write(r.stdout + r.stderr)
             if r.returncode != 0:
                 raise RuntimeError("nvcc failed: " + " ".join(cmd))
-    libdir = _cuda_lib_dir(nvcc)
     tmp = LIB + ".tmp"
-    link = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-L", libdir, "-lcufft", "-Xlinker", "-rpath," + libdir]
+    link = [nvcc, "-shared", "-o", tmp] + objs + ARCH
     r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)

@@ -139,6 +139,7 @@ dftu_status dftu_create(dftu_handle* out, const dftu_grid* grid, int nk, const d
     if (e == cudaSuccess) e = cudaMemset(st, 0, sizeof(int));
     if (e == cudaSuccess) e = upload(c, &one, std::vector<double>{1.0, 0.0});
     if (e == cudaSuccess) e = dalloc(c, &c->d_taylor, 2 * MAX_TAYLOR);
+    if (e == cudaSuccess) e = dalloc(c, &c->d_sink, 1);
     if (e != cudaSuccess) {
         for (void* p : c->allocs) cudaFree(p);
         delete c;
@@ -936,6 +937,25 @@ dftu_status dftu_get_results(dftu_handle h, double* n_out, double* U, double* J,
     if (e == cudaSuccess && EU_atom) e = cudaMemcpy(EU_atom, c->v.E, na * sizeof(double), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && EU_total) e = cudaMemcpy(EU_total, c->v.Etot, sizeof(double), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "get_results");
+    return DFTU_OK;
+}
+
+dftu_status dftu_access_ceiling(dftu_handle h, void* psi, dftu_prec prec, int nbands, int64_t ld_band, int rmw,
+                                dftu_stream stream) {
+    NvtxRange nvtx_range("dftu_access_ceiling");
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c) return DFTU_ERR_INVALID_ARG;
+    if (!c->atoms_ready) return fail(c, DFTU_ERR_NOT_READY, "access_ceiling: call dftu_setup_atoms first");
+    if (!psi || (prec != DFTU_C128 && prec != DFTU_C64) || !valid_stride_args(c, nbands, ld_band) || (rmw != 0 && rmw != 1))
+        return fail(c, DFTU_ERR_INVALID_ARG, "access_ceiling: null psi, bad precision, band count, ld_band or mode");
+    Guard g(c->device);
+    int64_t sk, ss, sn;
+    strides(c, nbands, ld_band, sk, ss, sn);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!gpu_addressable(c->device, psi, st)) return fail(c, DFTU_ERR_INVALID_ARG, "access_ceiling: the states are not addressable by this GPU");
+    cudaError_t e = launch_access_ceiling(c->v, psi, prec, nbands, sk, ss, sn, rmw, c->d_sink, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "access_ceiling");
+    c->last_stream = st;
     return DFTU_OK;
 }
 

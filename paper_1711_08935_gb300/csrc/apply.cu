@@ -20,7 +20,7 @@ struct ApplyArgs {
     int accumulate;        // 1: psi += c V_U psi_proj ; 0: psi = c V_U psi_proj on the sphere points
 };
 
-enum APol { A_F64 = 0, A_PAIR = 1, A_F32 = 2 };
+enum APol { A_F64 = 0, A_PAIR = 1, A_F32 = 2, A_F32P = 3 };   // A_F32P: complex64, paired orbital rows
 
 // (hi, lo) float split of a double (round-to-nearest hi, exact-ish remainder) -- used only for the
 // per-CTA coefficients, so the FP64 conversion cost is negligible.
@@ -211,6 +211,53 @@ __device__ __forceinline__ void apply_body(const Tile& t, const ApplyArgs& a, in
                 if (i < t.np) row[s_idx[i]] = x[u];
             }
         }
+    } else if (POL == A_F32P) {
+        // Orbital rows [hi_0 .. hi_{MP-1}] per point (MP = M rounded up to even, zero padded): one 8-byte
+        // shared load feeds two orbitals, whose real and imaginary coefficients sit in float pairs.
+        constexpr int MP = (M + 1) & ~1, NP = MP / 2;
+        float2* row = reinterpret_cast<float2*>(a.psi) + off;
+        const float* s_phf = reinterpret_cast<const float*>(after_c);
+        const float2* s_c = reinterpret_cast<const float2*>(after_idx);
+        float2 cre[NP], cim[NP];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            const float2 c0 = s_c[bl * MAXM + 2 * j];
+            const float2 c1 = (2 * j + 1 < M) ? s_c[bl * MAXM + 2 * j + 1] : make_float2(0.f, 0.f);
+            cre[j] = make_float2(c0.x, c1.x);
+            cim[j] = make_float2(c0.y, c1.y);
+        }
+        for (int i0 = q; i0 < t.np; i0 += Q * U) {
+            float2 x[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                int i = i0 + u * Q;
+                x[u] = (i < t.np && (a.accumulate || !s_first[i])) ? row[s_idx[i]] : make_float2(0.f, 0.f);
+            }
+            if (PF) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    int i = i0 + Q * U + u * Q;
+                    if (i < t.np) asm volatile("prefetch.global.L2 [%0];" ::"l"(row + s_idx[i]));
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const float* ph = s_phf + (i0 + u * Q) * MP;
+                float2 ar = make_float2(0.f, 0.f), ai = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < NP; ++j) {
+                    const float2 f2 = *reinterpret_cast<const float2*>(ph + 2 * j);
+                    ar = __ffma2_rn(f2, cre[j], ar);
+                    ai = __ffma2_rn(f2, cim[j], ai);
+                }
+                x[u] = __fadd2_rn(x[u], make_float2(ar.x + ar.y, ai.x + ai.y));
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                int i = i0 + u * Q;
+                if (i < t.np) row[s_idx[i]] = x[u];
+            }
+        }
     } else {
         float2* row = reinterpret_cast<float2*>(a.psi) + off;
         const float4* s_phi = reinterpret_cast<const float4*>(after_c);
@@ -287,6 +334,13 @@ __device__ __forceinline__ void apply_item(const View& v, const ApplyArgs& a, in
     if (POL == A_F64) {
         double* s_phi = reinterpret_cast<double*>(after_c);
         for (int e = threadIdx.x; e < TILE_PAD * M; e += CTA) s_phi[e] = (e < t.np * M) ? v.phi64[t.phi0 + e] : 0.0;
+    } else if (POL == A_F32P) {
+        float* s_phf = reinterpret_cast<float*>(after_c);
+        const int MP = (M + 1) & ~1;
+        for (int e = threadIdx.x; e < TILE_PAD * MP; e += CTA) {
+            const int i = e / MP, m = e - i * MP;
+            s_phf[e] = (i < t.np && m < M) ? v.phi_hi[t.phi0 + (int64_t)i * M + m] : 0.f;
+        }
     } else {
         float4* s_phi = reinterpret_cast<float4*>(after_c);
         int pe = -200;
@@ -410,8 +464,9 @@ static cudaError_t run_apply(const View& v, ApplyArgs a, const int* color_order,
 // The shapes selectable with dftu_set_kernel_variant, listed once for the single-system and the batched
 // launches: X(variant, lanes per band Q, band groups per CTA, points in flight per lane, L2 prefetch).
 // Variant 0, and 6 and 7, take the default case of each switch.
-#define DFTU_APPLY_SHAPES_F32(X) X(1, 8, 4, 4, 1) X(2, 16, 4, 8, 1) X(3, 16, 4, 4, 0) X(4, 8, 4, 8, 0) X(5, 16, 4, 4, 1)
-#define DFTU_APPLY_DEFAULT_F32 8, 4, 8, 1
+#define DFTU_APPLY_SHAPES_F32(X) X(1, A_F32, 8, 4, 8, 1) X(2, A_F32, 16, 4, 8, 1) X(3, A_F32P, 8, 4, 8, 1) \
+    X(4, A_F32P, 8, 4, 16, 1) X(5, A_F32P, 16, 4, 4, 1)
+#define DFTU_APPLY_DEFAULT_F32 A_F32P, 16, 4, 8, 1
 #define DFTU_APPLY_SHAPES_PAIR(X) X(1, 8, 4, 4, 1) X(2, 16, 4, 2, 1) X(3, 8, 4, 8, 1) X(4, 16, 2, 4, 1) X(5, 16, 4, 4, 0)
 #define DFTU_APPLY_DEFAULT_PAIR 16, 4, 4, 1
 
@@ -424,12 +479,12 @@ cudaError_t launch_apply(const View& v, void* psi, dftu_prec prec, dftu_f64_mode
         if (mode == DFTU_F64_NATIVE) return run_apply<A_F64, 8, 4, 4, 0, 1>(v, a, color_order, color_beg, st);
         return run_apply<A_PAIR, 8, 4, 4, 1, 1>(v, a, color_order, color_beg, st);
     }
-#define DFTU_CASE_F32(i, Q, NBG, U, PF) case i: return run_apply<A_F32, Q, NBG, U, PF>(v, a, color_order, color_beg, st);
+#define DFTU_CASE_F32(i, POL, Q, NBG, U, PF) case i: return run_apply<POL, Q, NBG, U, PF>(v, a, color_order, color_beg, st);
 #define DFTU_CASE_PAIR(i, Q, NBG, U, PF) case i: return run_apply<A_PAIR, Q, NBG, U, PF>(v, a, color_order, color_beg, st);
     if (prec == DFTU_C64) {
         switch (variant) {
             DFTU_APPLY_SHAPES_F32(DFTU_CASE_F32)
-            default: return run_apply<A_F32, DFTU_APPLY_DEFAULT_F32>(v, a, color_order, color_beg, st);
+            default: return run_apply<DFTU_APPLY_DEFAULT_F32>(v, a, color_order, color_beg, st);
         }
     }
     if (mode == DFTU_F64_NATIVE) return run_apply<A_F64, 8, 4, 4, 0>(v, a, color_order, color_beg, st);
@@ -535,12 +590,12 @@ static cudaError_t run_apply_batch(const BatchLaunch& b, const double* coef, int
 
 cudaError_t launch_apply_batch(const BatchLaunch& b, dftu_prec prec, dftu_f64_mode mode, int variant, const double* coef,
                                int accumulate, cudaStream_t st) {
-#define DFTU_CASE_F32(i, Q, NBG, U, PF) case i: return run_apply_batch<A_F32, Q, NBG, U, PF>(b, coef, accumulate, st);
+#define DFTU_CASE_F32(i, POL, Q, NBG, U, PF) case i: return run_apply_batch<POL, Q, NBG, U, PF>(b, coef, accumulate, st);
 #define DFTU_CASE_PAIR(i, Q, NBG, U, PF) case i: return run_apply_batch<A_PAIR, Q, NBG, U, PF>(b, coef, accumulate, st);
     if (prec == DFTU_C64) {
         switch (variant) {
             DFTU_APPLY_SHAPES_F32(DFTU_CASE_F32)
-            default: return run_apply_batch<A_F32, DFTU_APPLY_DEFAULT_F32>(b, coef, accumulate, st);
+            default: return run_apply_batch<DFTU_APPLY_DEFAULT_F32>(b, coef, accumulate, st);
         }
     }
     if (mode == DFTU_F64_NATIVE) return run_apply_batch<A_F64, 8, 4, 4, 0>(b, coef, accumulate, st);

@@ -163,6 +163,7 @@ struct Ctx {
     double* d_forces = nullptr;      // [natoms][3]
     double* d_current = nullptr;     // [natoms][3] per-atom Hubbard current
     double* d_fll = nullptr;         // [natoms][2] E_ee, E_DC of App. A
+    int* d_sink = nullptr;           // [1] output of the access-ceiling pass
     std::vector<int> h_coul_set;     // host copies, so hot-path calls never read the device
     std::vector<double> h_fixU;
 };
@@ -214,6 +215,10 @@ cudaError_t launch_apply(const View& v, void* psi, dftu_prec prec, dftu_f64_mode
 cudaError_t launch_gauge_phases(const View& v, const double* A, cudaStream_t st);
 // cv = V p for the first nbands bands (the coefficients the apply scatters).
 cudaError_t launch_coefvec(const View& v, int nbands, cudaStream_t st);
+// One pass of the access pattern alone: read (rmw = 0) or read and write back unchanged (rmw = 1) every
+// sphere point of the states, no arithmetic; sink: one device int the read pass may write.
+cudaError_t launch_access_ceiling(const View& v, void* psi, dftu_prec prec, int nbands, int64_t sk, int64_t ss, int64_t sn,
+                                  int rmw, int* sink, cudaStream_t st);
 cudaError_t launch_coefvec_batch(const BatchLaunch& b, cudaStream_t st);
 // Taylor step in the span of the orbitals: cv = sum_{j=1}^{order} c_j V p_{j-1}, p_0 = p, p_j = c_j O V p_{j-1}
 // (O: the block overlap above), coefs = the order complex c_j on the device.

@@ -35,7 +35,7 @@ EXPORTED = ["dftu_create", "dftu_setup_atoms", "dftu_get_sphere", "dftu_coulomb_
             "dftu_batch_occupations", "dftu_batch_acbn0_uj", "dftu_batch_apply", "dftu_batch_last_error",
             "dftu_batch_destroy", "dftu_forces", "dftu_radius_cell", "dftu_radius_threshold",
             "dftu_set_vector_potential", "dftu_hubbard_current", "dftu_fll_energy", "dftu_occupation_elems",
-            "dftu_export_occupations", "dftu_import_occupations"]
+            "dftu_export_occupations", "dftu_import_occupations", "dftu_access_ceiling"]
 
 
 class DftuGrid(C.Structure):
@@ -109,6 +109,7 @@ def load() -> C.CDLL:
         "dftu_occupation_elems": [vp],
         "dftu_export_occupations": [vp, vp, vp],
         "dftu_import_occupations": [vp, vp, vp],
+        "dftu_access_ceiling": [vp, vp, i32, i32, i64, i32, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -260,6 +261,13 @@ class Handle:
 
     def occupations(self, f: torch.Tensor, stream=None):
         self._check(self.lib.dftu_occupations(self.h, self._f_arg(f), _stream_ptr(stream, self.device)))
+
+    def access_ceiling(self, psi: torch.Tensor, rmw: bool = False, stream=None):
+        """One pass of the access pattern alone (dftu_access_ceiling): read every sphere point of psi, or
+        read and write each back unchanged; time it to bound the projection (read) and the apply (rmw)."""
+        prec, nb, ld = self._psi_args(psi)
+        self._check(self.lib.dftu_access_ceiling(self.h, C.c_void_p(psi.data_ptr()), prec, nb, ld, 1 if rmw else 0,
+                                                 _stream_ptr(stream, self.device)))
 
     def occupation_sums(self, out: torch.Tensor = None, stream=None) -> torch.Tensor:
         """This handle's occupation sums (rho, Pbar) of the last occupations, as a float64 tensor on the
@@ -428,6 +436,13 @@ class Batch:
 
     def occupations(self, stream=None):
         self._check(self.lib.dftu_batch_occupations(self.b, _stream_ptr(stream, self.device)))
+
+    def access_ceiling(self, psi: torch.Tensor, rmw: bool = False, stream=None):
+        """One pass of the access pattern alone (dftu_access_ceiling): read every sphere point of psi, or
+        read and write each back unchanged; time it to bound the projection (read) and the apply (rmw)."""
+        prec, nb, ld = self._psi_args(psi)
+        self._check(self.lib.dftu_access_ceiling(self.h, C.c_void_p(psi.data_ptr()), prec, nb, ld, 1 if rmw else 0,
+                                                 _stream_ptr(stream, self.device)))
 
     def occupation_sums(self, out: torch.Tensor = None, stream=None) -> torch.Tensor:
         """This handle's occupation sums (rho, Pbar) of the last occupations, as a float64 tensor on the

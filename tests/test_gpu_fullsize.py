@@ -153,4 +153,17 @@ def test_full_size_pass_every_shape(workload):
             upd_scale = max(np.max(np.abs(j * deltas[key])), 1e-5 * np.max(np.abs(row)))
             assert np.max(np.abs((got - row) - j * deltas[key])) < 1e-10 * upd_scale, (v, key)
             assert rel(got, row + j * deltas[key]) < 1e-12, (v, key)
+
+    # ---- apply of complex64 states: every shape in turn on the same projections and potential, sampled
+    # rows against their FP32 start plus j times the oracle's update (FP32 sums, one rounding per apply)
+    psi32 = psi.to(torch.complex64)
+    start32 = {key: psi32[key].to(torch.complex128).cpu().numpy() for key in w["samples"]}
+    for j, v in enumerate(range(h.lib.dftu_kernel_variants(3)), start=1):
+        h.set_kernel_variant(3, v)
+        h.apply(psi32)
+        for key in w["samples"]:
+            got = psi32[key].to(torch.complex128).cpu().numpy()
+            assert rel(got, start32[key] + j * deltas[key]) < 2e-6, (v, key)
+    del psi32
+    torch.cuda.empty_cache()
     h.close()

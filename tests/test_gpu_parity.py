@@ -334,3 +334,22 @@ def test_hubbard_forces_match_oracle(dtype):
     F = h.forces(g, fd)
     assert np.max(np.abs(F - Fref)) < (1e-12 if dtype == torch.complex128 else 2e-6) * np.max(np.abs(Fref))
     assert np.max(np.abs(Fref)) > 1e-5
+
+
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+def test_access_ceiling_pass_leaves_states_unchanged(dtype):
+    """dftu_access_ceiling reads (and in its read-modify-write form writes back) every sphere point of the
+    states without changing any value, for collinear and non-collinear layouts."""
+    for s, nb in ((C.periodic_two_atoms(), 9), (synth.small_oxide_system(), 70)):
+        psi = torch.from_numpy(C.states_np(s, nb, seed=3)).cuda().to(dtype)
+        ref = psi.clone()
+        h = dftu.handle_for_system(s, nb)
+        h.access_ceiling(psi, rmw=False)
+        h.access_ceiling(psi, rmw=True)
+        torch.cuda.synchronize()
+        assert torch.equal(psi, ref)
+        assert h.sync_status() == dftu.DFTU_OK
+        h.close()
+    h = dftu.handle_for_system(C.periodic_two_atoms(), 4)
+    assert h.lib.dftu_access_ceiling(h.h, None, 0, 4, 8000, 0, None) == dftu.DFTU_ERR_INVALID_ARG
+    h.close()
