@@ -34,13 +34,13 @@ WORKLOAD = "oxide supercell 96^3 h=0.25, 8 TM(3d,R4.5)+8 O(2p,R3.5), 256 bands, 
 
 # DRAM bytes per state (one band of one k-point and spin) measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum) on the 64-band oxide case for the kernel variants named here; see
-# profiles/pair_project_apply_oxide_small.md.  Valid only while that variant is the one timed.
-NCU_TRAFFIC_PER_STATE = {("project", 1): (808.521472e6 + 13.469184e6) / 128,
-                         ("apply", 4): (806.894080e6 + 573.875200e6) / 128}
+# profiles/project_apply_oxide_small.md.  Valid only while that variant is the one timed.
+NCU_TRAFFIC_PER_STATE = {("project", 0): (808.50e6 + 11.11e6) / 128,
+                         ("apply", 0): (800.74e6 + 566.71e6) / 128}
 # The same for the fixed complex128 shapes of the gauge-invariant path; see
 # profiles/gauge_project_apply_current_oxide_small.md.
 NCU_TRAFFIC_PER_STATE_GAUGE = {"project": (815.383808e6 + 7.759104e6) / 128,
-                               "apply": (816.965376e6 + 576.625664e6) / 128}
+                               "apply": None}   # the gauge apply changed (precomputed coefficients) after that capture
 
 
 def measured_peaks():
@@ -917,8 +917,10 @@ def run_gauge(args):
                    "sphere_points": int(sum(npts)), "l2": "inputs (58 GB of states) far larger than L2; no flush needed"},
         "roofline": {"bound": "hbm", "kernel": "apply (gauge)" if dom_is_apply else "project (gauge)",
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "peak_source": src, "traffic": round(NCU_TRAFFIC_PER_STATE_GAUGE["apply" if dom_is_apply else "project"]
-                                                          * nb * s.nk * 2), "bytes_per_launch": dom_b},
+                     "peak_source": src, "traffic": (round(NCU_TRAFFIC_PER_STATE_GAUGE["apply" if dom_is_apply else "project"]
+                                                           * nb * s.nk * 2)
+                                                     if NCU_TRAFFIC_PER_STATE_GAUGE["apply" if dom_is_apply else "project"]
+                                                     else None), "bytes_per_launch": dom_b},
         "kernels_ms": {"project_gauge": round(pr_g, 4), "apply_gauge": round(ap_g, 4), "project_plain": round(pr_plain, 4),
                        "apply_plain": round(ap_plain, 4)},
         "plain_pass_ms": round(ms_plain, 4), "gauge_overhead": round(ms_g / ms_plain, 3),

@@ -304,7 +304,7 @@ __device__ __forceinline__ void proj_body_pair(const View& v, const Tile& t, int
                 int i = i0 + c * Q;
                 x[c] = (i < t.np) ? __ldg(row + s_idx[i]) : make_double2(0.0, 0.0);
             }
-            if (PF) {
+            if (PF == 1 || (PF == 2 && (q == 0 || q == Q - 1))) {   // PF == 2: the group's edge lanes only
 #pragma unroll
                 for (int c = 0; c < CH; ++c) {
                     int i = i0 + Q * CH + c * Q;
@@ -430,7 +430,7 @@ __device__ __forceinline__ void proj_body_pair2(const View& v, const Tile& t, in
                 int i = i0 + c * Q;
                 x[c] = (i < t.np) ? __ldg(row + s_idx[i]) : make_double2(0.0, 0.0);
             }
-            if (PF) {
+            if (PF == 1 || (PF == 2 && (q == 0 || q == Q - 1))) {   // PF == 2: the group's edge lanes only
 #pragma unroll
                 for (int c = 0; c < CH; ++c) {
                     int i = i0 + Q * CH + c * Q;
@@ -573,12 +573,16 @@ __device__ __forceinline__ void proj_body_f32x2(const View& v, const Tile& t, in
                 x1[c] = (in && row1) ? __ldg(row1 + g) : make_float2(0.f, 0.f);
             }
             if (PF) {
+                // PF == 2: only the first and last lane of a band's group, whose points bound the Q
+                // consecutive points the group reads next (at most two 128-byte lines per row)
+                if (PF == 1 || q == 0 || q == Q - 1) {
 #pragma unroll
-                for (int c = 0; c < CH; ++c) {
-                    const int i = i0 + Q * CH + c * Q;
-                    if (i < t.np) {
-                        prefetch_l2(row0 + s_idx[i]);
-                        if (row1) prefetch_l2(row1 + s_idx[i]);
+                    for (int c = 0; c < CH; ++c) {
+                        const int i = i0 + Q * CH + c * Q;
+                        if (i < t.np) {
+                            prefetch_l2(row0 + s_idx[i]);
+                            if (row1) prefetch_l2(row1 + s_idx[i]);
+                        }
                     }
                 }
             }
@@ -886,11 +890,11 @@ static cudaError_t run_project(const View& v, const ProjArgs& a, cudaStream_t st
 // arithmetic with paired orbitals, P_F32B2 the complex64 form with two bands per lane.
 #define DFTU_PROJECT_SHAPES_F32(X) \
     X(1, P_F32, 8, 16, 8, 0, 2) X(2, P_F32B2, 8, 8, 2, 0, 2) X(3, P_F32B2, 8, 8, 8, 0, 2) X(4, P_F32B2, 4, 16, 2, 0, 2) \
-    X(5, P_F32B2, 16, 8, 4, 0, 2) X(6, P_F32B2, 8, 12, 4, 0, 2) X(7, P_F32B2, 8, 8, 4, 0, 3)
+    X(5, P_F32B2, 16, 8, 4, 0, 2) X(6, P_F32B2, 8, 8, 4, 2, 2) X(7, P_F32B2, 16, 8, 4, 2, 2)
 #define DFTU_PROJECT_DEFAULT_F32 P_F32B2, 8, 8, 4, 0, 2
 #define DFTU_PROJECT_SHAPES_PAIR(X) \
-    X(1, P_PAIR, 4, 8, 4, 1, 2) X(2, P_PAIR, 4, 8, 4, 0, 2) X(3, P_PAIR2, 4, 8, 8, 1, 2) X(4, P_PAIR, 4, 16, 4, 1, 2) \
-    X(5, P_PAIR, 8, 8, 4, 1, 2) X(6, P_PAIR, 4, 4, 8, 1, 2) X(7, P_PAIR, 8, 16, 4, 1, 2)
+    X(1, P_PAIR, 4, 8, 4, 1, 2) X(2, P_PAIR, 4, 8, 4, 0, 2) X(3, P_PAIR2, 4, 8, 8, 1, 2) X(4, P_PAIR, 4, 8, 8, 2, 2) \
+    X(5, P_PAIR, 8, 8, 4, 1, 2) X(6, P_PAIR, 8, 8, 4, 2, 2) X(7, P_PAIR, 8, 16, 4, 1, 2)
 #define DFTU_PROJECT_DEFAULT_PAIR P_PAIR, 4, 8, 8, 1, 2
 
 cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_f64_mode mode, int nbands,

@@ -136,6 +136,37 @@ def test_gauge_taylor_step_matches_oracle():
     h.close()
 
 
+@pytest.mark.parametrize("name", ["periodic_self_overlap", "overlapping_three_atoms"])
+def test_gauge_taylor_steps_with_overlapping_spheres_match_oracle(name):
+    """Three real-time steps with V_U^A where spheres overlap each other or their own images: the step's
+    overlap blocks between different atoms and images carry the phases exp(+i A.(d_a - d_b)) and
+    exp(+i k.(T_a - T_b) L); against the term-by-term Taylor series of the oracle's gauge operator."""
+    s = SYSTEMS[name]()
+    st = O.setup_atoms(s)
+    nb, dt, order = 5, 0.35, 4
+    psi = C.states_np(s, nb, seed=8)
+    ns = psi.shape[1]
+    f = np.linspace(1.0, 0.3, nb)[None, None, :].repeat(s.nk, 0).repeat(ns, 1)
+    U = _fixed_u(s)
+    dev = torch.device("cuda:0")
+    h = _gpu_handle(s, nb, U)
+    h.set_vector_potential(torch.tensor(A_VEC, dtype=torch.float64, device=dev))
+    t = torch.from_numpy(psi).to(dev)
+    fd = torch.from_numpy(f).to(dev)
+    ref = psi.copy()
+    for step in range(3):
+        _, _, V, _ = _oracle_gauge_pass(s, st, ref, f, U, A_VEC)
+        out, term = ref.copy(), ref
+        for j in range(1, order + 1):
+            pj = O.project_gauge(s, st, term, A_VEC)
+            term = (-1j * dt / j) * O.apply_gauge(s, st, np.zeros_like(term), pj, V, A_VEC)
+            out = out + term
+        ref = out
+        h.taylor_step(t, None, fd, dt, order)
+        assert rel(t.cpu().numpy(), ref) < 1e-12, step
+    h.close()
+
+
 def test_vector_potential_in_cuda_graph_follows_device_A():
     """A graph that captures dftu_set_vector_potential + dftu_taylor_step reads A from device memory at each
     replay: replays after A changes equal eager steps with the new A."""
