@@ -738,6 +738,12 @@ def run_molecules(args):
     clocks.start()
     clocks.mark()
     ms_b = time_it(batched, args.steps, args.warmup)
+    # where a batched pass spends its time (CUDA events between the calls of one pass, after the timed ones)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    evs[0].record(); batch.project(); evs[1].record(); batch.occupations(); evs[2].record()
+    batch.acbn0_uj(); evs[3].record(); batch.apply(cdt); evs[4].record()
+    torch.cuda.synchronize()
+    phases = {n: round(evs[i].elapsed_time(evs[i + 1]), 4) for i, n in enumerate(("project", "occupations", "acbn0", "apply"))}
     clocks.mark()
     clk = clocks.stop()
     ms_1 = time_it(lambda: one_by_one(allidx, psis), max(1, args.steps // 2), 1)
@@ -766,6 +772,7 @@ def run_molecules(args):
                                "Gamma, collinear), one persistent launch per streaming kernel",
                    "atoms": sum(len(s.atoms) for s in systems), "sphere_points": sum(S), "states": 2 * sum(nbs)},
         "one_by_one_c64_ms": round(ms_1, 3), "batched_speedup_vs_one_by_one_c64": round(ms_1 / ms_b, 3),
+        "batched_phases_ms": phases,
         "subset64": {"systems": len(sub), "one_by_one_c128_ms": round(ms_sub64, 3), "batched_c128_ms": round(ms_sub64_b, 3),
                      "batched_c64_ms": round(ms_sub32_b, 3),
                      "batched_c64_speedup_vs_one_by_one_fp64": round(ms_sub64 / ms_sub32_b, 3),
