@@ -140,7 +140,7 @@ dftu_status dftu_batch_bind(dftu_batch b, const void* const* psi, dftu_prec prec
         }
         args[s] = a;
         max_reduce = std::max<int64_t>(max_reduce, (int64_t)c->nk * c->ns * nbands[s] * c->MT);
-        max_rows = std::max(max_rows, (c->spin == DFTU_NONCOLLINEAR ? c->nk : c->nk * c->ns) * nbands[s]);
+        max_rows = std::max(max_rows, (c->spin == DFTU_NONCOLLINEAR ? c->nk : c->nk * c->ns) * nbands[s] * c->nspecies);
     }
     int prev = -1;
     cudaGetDevice(&prev);

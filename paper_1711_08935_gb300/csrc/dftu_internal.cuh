@@ -189,7 +189,7 @@ struct BatchLaunch {
     int nsys;
     int maxM;
     int64_t max_reduce;       // max over systems of (k*spin rows) * nbands * sum M
-    int max_rows_nbar;        // max over systems of rows * nbands for Nbar
+    int max_rows_nbar;        // max over systems of rows * nbands * species (the Nbar threads)
     int max_atoms, max_ns;
 };
 

@@ -11,11 +11,14 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ double2 cmulc(double2 a, double2 b) { return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y); }  // a conj(b)
 
 // Eq. (9): Nbar per state = sum over atoms of the state's species-mates and m (and spinor components) of |p|^2.
+// One thread per (state, species).
 __device__ __forceinline__ void nbar_elem(const View& v, int nbands, int64_t g) {
     int rows = v.noncollinear ? v.nk : v.nk * v.ns;
-    if (g >= (int64_t)rows * nbands) return;
+    if (g >= (int64_t)rows * nbands * v.nspecies) return;
+    const int sp = (int)(g % v.nspecies);
+    g /= v.nspecies;
     int row = (int)(g / nbands), band = (int)(g % nbands);
-    for (int sp = 0; sp < v.nspecies; ++sp) {
+    {
         double acc = 0.0;
         for (int a = 0; a < v.natoms; ++a) {
             if (v.atom_species[a] != sp) continue;
@@ -130,10 +133,10 @@ __device__ __forceinline__ double warp_sum(double x) {
 }
 
 // Eqs. (10)-(11) [collinear/unpolarised] or (B5)-(B6) [non-collinear], then Eq. (3)/(A5) and Eq. (6).
-// One warp per atom; sums are lane-strided then tree-reduced (fixed order).
-__device__ __forceinline__ void acbn0_block(const View& v) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int a = warp; a < v.natoms; a += nw) {
+// One warp per atom (atoms warp0, warp0 + nw, ...); sums are lane-strided then tree-reduced (fixed order).
+__device__ __forceinline__ void acbn0_atoms(const View& v, int warp0, int nw) {
+    const int lane = threadIdx.x & 31;
+    for (int a = warp0; a < v.natoms; a += nw) {
         const int M = v.atom_M[a], sp = v.atom_species[a];
         const int64_t mo = v.atom_mat_off[a];
         const double* Vc = v.coul + v.species_coul_off[sp];
@@ -252,17 +255,31 @@ __device__ __forceinline__ void acbn0_block(const View& v) {
             if (zero) atomicOr(v.status, ST_ZERO_DENOM);
         }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int a = 0; a < v.natoms; ++a) s += v.E[a];
-        v.Etot[0] = s;
-    }
 }
 
-__global__ void __launch_bounds__(1024) k_acbn0(View v) { acbn0_block(v); }
+// E_U summed over atoms in atom order.
+__device__ __forceinline__ void energy_total(const View& v) {
+    double s = 0.0;
+    for (int a = 0; a < v.natoms; ++a) s += v.E[a];
+    v.Etot[0] = s;
+}
 
-__global__ void __launch_bounds__(256) k_acbn0_batch(const View* __restrict__ views) { acbn0_block(views[blockIdx.x]); }
+constexpr int ACBN0_WARPS = 4;   // atoms per CTA of k_acbn0 (one warp each)
+
+__global__ void __launch_bounds__(32 * ACBN0_WARPS) k_acbn0(View v) {
+    acbn0_atoms(v, blockIdx.x * ACBN0_WARPS + (threadIdx.x >> 5), gridDim.x * ACBN0_WARPS);
+}
+
+__global__ void k_energy_total(View v) {
+    if (threadIdx.x == 0) energy_total(v);
+}
+
+__global__ void __launch_bounds__(256) k_acbn0_batch(const View* __restrict__ views) {
+    const View& v = views[blockIdx.x];
+    acbn0_atoms(v, threadIdx.x >> 5, blockDim.x >> 5);
+    __syncthreads();
+    if (threadIdx.x == 0) energy_total(v);
+}
 
 // Hubbard forces (Sec. IV, state-gradient form, U_eff fixed): one CTA per (atom, direction),
 // F = -sum_{blocks} sum_{ab} V_ab sum_{k,n} w f [conj(g_a) p_b + conj(p_a) g_b], g = <phi|d_i psi>.
@@ -385,8 +402,8 @@ cudaError_t launch_fll(const View& v, double* out, cudaStream_t st) {
 
 cudaError_t launch_nbar(const View& v, int nbands, cudaStream_t st) {
     int rows = v.noncollinear ? v.nk : v.nk * v.ns;
-    int64_t n = (int64_t)rows * nbands;
-    k_nbar<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(v, nbands);
+    int64_t n = (int64_t)rows * nbands * v.nspecies;
+    k_nbar<<<(unsigned)((n + 63) / 64), 64, 0, st>>>(v, nbands);
     return cudaGetLastError();
 }
 
@@ -397,13 +414,16 @@ cudaError_t launch_occupations(const View& v, const double* f, int nbands, cudaS
 }
 
 cudaError_t launch_acbn0(const View& v, cudaStream_t st) {
-    k_acbn0<<<1, 1024, 0, st>>>(v);
+    k_acbn0<<<(v.natoms + ACBN0_WARPS - 1) / ACBN0_WARPS, 32 * ACBN0_WARPS, 0, st>>>(v);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_energy_total<<<1, 32, 0, st>>>(v);
     return cudaGetLastError();
 }
 
 cudaError_t launch_occupations_batch(const BatchLaunch& b, cudaStream_t st) {
-    dim3 g1((unsigned)((b.max_rows_nbar + 255) / 256), b.nsys);
-    k_nbar_batch<<<g1, 256, 0, st>>>(b.views, b.args);
+    dim3 g1((unsigned)((b.max_rows_nbar + 63) / 64), b.nsys);
+    k_nbar_batch<<<g1, 64, 0, st>>>(b.views, b.args);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     dim3 g2(b.max_atoms, b.max_ns * OCC_SPLIT, b.nsys);
