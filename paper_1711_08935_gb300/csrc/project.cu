@@ -56,10 +56,11 @@ __device__ __forceinline__ float pow2f(int e) {   // 2^e as float for e in [-126
 }
 
 // Tile partial sum, before the Bloch phase and dV (k_tile_reduce applies both once per image segment).
-// poff: offset of the direction's slice (three-table projections), 0 otherwise.
+// Layout [k*spin][tile slot (moff + m)][band], band fastest, so the reduce reads 32 bands of one slot in
+// one coalesced access.  poff: offset of the direction's slice (three-table projections), 0 otherwise.
 __device__ __forceinline__ void write_partial(const View& v, const Tile& t, int ks, int band, int m, double re, double im,
                                               int64_t poff) {
-    v.part[poff + ((int64_t)ks * v.max_bands + band) * v.TM + t.moff + m] = make_double2(re, im);
+    v.part[poff + ((int64_t)ks * v.TM + t.moff + m) * v.max_bands + band] = make_double2(re, im);
 }
 
 // Exact float -> double times 2^s with integer operations (the conversion instruction runs on the
@@ -820,17 +821,18 @@ bool smem_configured(const void* fn, int bytes) {
     return false;
 }
 
-// p[ks][band][moff_I + m] = sum over the atom's tiles (fixed order) of the tile partials.
+// p[ks][band][moff_I + m] = sum over the atom's tiles (fixed order) of the tile partials; one thread per
+// (k*spin, orbital slot, band), band fastest.
 __device__ __forceinline__ void tile_reduce_elem(const View& v, int nbands, int64_t g) {
-    int64_t rows = (int64_t)v.nk * v.ns * nbands;
-    if (g >= rows * v.MT) return;
-    int64_t rowi = g / v.MT;
-    int j = (int)(g % v.MT);
-    int ks = (int)(rowi / nbands), band = (int)(rowi % nbands);
-    int a = 0;
-    while (a + 1 < v.natoms && v.atom_moff[a + 1] <= j) ++a;
-    int m = j - v.atom_moff[a];
-    const double2* prow = v.part + ((int64_t)ks * v.max_bands + band) * v.TM;
+    if (g >= (int64_t)v.nk * v.ns * v.MT * nbands) return;
+    const int band = (int)(g % nbands);
+    const int64_t r = g / nbands;
+    const int j = (int)(r % v.MT);
+    const int ks = (int)(r / v.MT);
+    const int a = v.orb_atom[j];
+    const int m = j - v.atom_moff[a];
+    const double2* pks = v.part + (int64_t)ks * v.TM * v.max_bands + band;
+    auto prow_at = [&](int slot) { return pks[(int64_t)slot * v.max_bands]; };
     const int k = ks / v.ns;
     // tiles of one image segment are consecutive: sum them, then apply that segment's Bloch phase
     double re = 0.0, im = 0.0, sr = 0.0, si = 0.0;
@@ -846,7 +848,7 @@ __device__ __forceinline__ void tile_reduce_elem(const View& v, int nbands, int6
             seg = tl.seg;
             sr = si = 0.0;
         }
-        const double2 x = prow[tl.moff + m];
+        const double2 x = prow_at(tl.moff + m);
         sr += x.x;
         si += x.y;
     }
