@@ -550,16 +550,21 @@ __device__ __forceinline__ void proj_body_pair2(const View& v, const Tile& t, in
 // from shared memory serves both.  Products are compensated as in proj_body_f32 (phi = hi + lo, both
 // halves multiplied by the FP32 state value); the sums are plain FP32 over the lane's points of the
 // tile, then over the Q lanes, and FP64 from there on (across tiles).
-template <int M, int Q, int CH, int PF>
+// FOLD: each product phi x is formed from both halves of phi by two fused multiply-adds into one FP32 sum
+// (hi then lo), instead of separate sums of the hi and lo products: half the accumulator registers, the
+// same products; the lo half then enters at the sum's rounding, which plain FP32 accumulation over a
+// lane's points already sets.
+template <int M, int Q, int CH, int PF, int FOLD = 0>
 __device__ __forceinline__ void proj_body_f32x2(const View& v, const Tile& t, int ks, int band, int nbands,
                                                 const float2* __restrict__ row0, const float2* __restrict__ row1,
                                                 const int* s_idx, const float* s_phf, int64_t poff) {
     constexpr int MP = (M + 1) & ~1, NP = MP / 2;
+    constexpr int NS = FOLD ? 2 : 4;
     const int q = threadIdx.x & (Q - 1);
-    // [band][part]: real hi, imaginary hi, real lo, imaginary lo of orbitals (2j, 2j+1)
-    float2 S0[4][NP], S1[4][NP];
+    // [band][part]: real hi, imaginary hi (real lo, imaginary lo unless folded) of orbitals (2j, 2j+1)
+    float2 S0[NS][NP], S1[NS][NP];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < NS; ++a)
 #pragma unroll
         for (int j = 0; j < NP; ++j) { S0[a][j] = make_float2(0.f, 0.f); S1[a][j] = S0[a][j]; }
     if (row0) {
@@ -596,10 +601,17 @@ __device__ __forceinline__ void proj_body_f32x2(const View& v, const Tile& t, in
                 for (int j = 0; j < NP; ++j) {
                     const float2 h2 = *reinterpret_cast<const float2*>(ph + 2 * j);
                     const float2 l2 = *reinterpret_cast<const float2*>(ph + MP + 2 * j);
-                    S0[0][j] = ffma2(h2, r0, S0[0][j]); S0[1][j] = ffma2(h2, m0, S0[1][j]);
-                    S0[2][j] = ffma2(l2, r0, S0[2][j]); S0[3][j] = ffma2(l2, m0, S0[3][j]);
-                    S1[0][j] = ffma2(h2, r1, S1[0][j]); S1[1][j] = ffma2(h2, m1, S1[1][j]);
-                    S1[2][j] = ffma2(l2, r1, S1[2][j]); S1[3][j] = ffma2(l2, m1, S1[3][j]);
+                    if (FOLD) {
+                        S0[0][j] = ffma2(l2, r0, ffma2(h2, r0, S0[0][j]));
+                        S0[1][j] = ffma2(l2, m0, ffma2(h2, m0, S0[1][j]));
+                        S1[0][j] = ffma2(l2, r1, ffma2(h2, r1, S1[0][j]));
+                        S1[1][j] = ffma2(l2, m1, ffma2(h2, m1, S1[1][j]));
+                    } else {
+                        S0[0][j] = ffma2(h2, r0, S0[0][j]); S0[1][j] = ffma2(h2, m0, S0[1][j]);
+                        S0[NS - 2][j] = ffma2(l2, r0, S0[NS - 2][j]); S0[NS - 1][j] = ffma2(l2, m0, S0[NS - 1][j]);
+                        S1[0][j] = ffma2(h2, r1, S1[0][j]); S1[1][j] = ffma2(h2, m1, S1[1][j]);
+                        S1[NS - 2][j] = ffma2(l2, r1, S1[NS - 2][j]); S1[NS - 1][j] = ffma2(l2, m1, S1[NS - 1][j]);
+                    }
                 }
             }
         }
@@ -607,7 +619,7 @@ __device__ __forceinline__ void proj_body_f32x2(const View& v, const Tile& t, in
 #pragma unroll
     for (int off = Q / 2; off > 0; off >>= 1)
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < NS; ++a)
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
                 S0[a][j] = fadd2(S0[a][j], make_float2(shfl_x(S0[a][j].x, off), shfl_x(S0[a][j].y, off)));
@@ -618,9 +630,9 @@ __device__ __forceinline__ void proj_body_f32x2(const View& v, const Tile& t, in
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
                 if (b == 1 && !row1) break;
-                float v4[4];
+                float v4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                for (int a = 0; a < 4; ++a) {
+                for (int a = 0; a < NS; ++a) {
                     const float2 w = (b == 0) ? S0[a][0] : S1[a][0];
                     v4[a] = w.x;
                 }
@@ -628,7 +640,7 @@ __device__ __forceinline__ void proj_body_f32x2(const View& v, const Tile& t, in
                 for (int m = 1; m < M; ++m)
                     if (m == mq)
 #pragma unroll
-                        for (int a = 0; a < 4; ++a) {
+                        for (int a = 0; a < NS; ++a) {
                             const float2 w = (b == 0) ? S0[a][m / 2] : S1[a][m / 2];
                             v4[a] = (m & 1) ? w.y : w.x;
                         }
@@ -643,15 +655,15 @@ __device__ __forceinline__ void proj_body_f32x2(const View& v, const Tile& t, in
 // ------------------------------------------------------------------------------------------------
 // kernels
 // ------------------------------------------------------------------------------------------------
-enum Pol { P_F64 = 0, P_PAIR = 1, P_F32 = 2, P_PAIR2 = 3, P_F32B2 = 4 };
+enum Pol { P_F64 = 0, P_PAIR = 1, P_F32 = 2, P_PAIR2 = 3, P_F32B2 = 4, P_F32B2F = 5 };
 
 // bands a lane carries at once
-template <int POL> struct LaneBands { static constexpr int value = (POL == P_F32B2) ? 2 : 1; };
+template <int POL> struct LaneBands { static constexpr int value = (POL == P_F32B2 || POL == P_F32B2F) ? 2 : 1; };
 
 // One work item: tile `tile_id` of the system described by (v, a), spin/component index ks, every band of
 // band chunk `chunk` (NBG groups of BPC bands), against orbital table `dir` (0 unless the launch projects
 // onto several tables).  The tile is staged in shared memory once.
-template <int POL, int Q, int CH, int NBG, int PF, int G>
+template <int POL, int Q, int CH, int NBG, int PF, int G, int NT = CTA>
 __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, int tile_id, int ks, int chunk,
                                              unsigned char* smem, int* s_pe, int dir = 0) {
     int* s_idx = reinterpret_cast<int*>(smem);
@@ -661,21 +673,21 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
     const int k = ks / v.ns, s = ks % v.ns;
     constexpr int NBL = LaneBands<POL>::value;   // bands per lane
     constexpr int BPW = (32 / Q) * NBL;
-    constexpr int BPC = (CTA / 32) * BPW;
+    constexpr int BPC = (NT / 32) * BPW;
 
     // ---- stage the tile once (grid indices, orbital rows, orbital exponent bound)
     if (threadIdx.x == 0) *s_pe = -200;
-    for (int i = threadIdx.x; i < TILE; i += CTA) s_idx[i] = (i < t.np) ? v.pt_idx[t.p0 + i] : 0;
+    for (int i = threadIdx.x; i < TILE; i += NT) s_idx[i] = (i < t.np) ? v.pt_idx[t.p0 + i] : 0;
     __syncthreads();
     if (POL == P_F64) {
         double* s_phi = reinterpret_cast<double*>(smem + TILE * sizeof(int));
-        for (int e = threadIdx.x; e < TILE * t.M; e += CTA)
+        for (int e = threadIdx.x; e < TILE * t.M; e += NT)
             s_phi[e] = (e < t.np * t.M) ? v.phi64[ph0 + e] : 0.0;
-    } else if (POL == P_F32 || POL == P_PAIR2 || POL == P_F32B2) {
+    } else if (POL == P_F32 || POL == P_PAIR2 || POL == P_F32B2 || POL == P_F32B2F) {
         float* s_phf = reinterpret_cast<float*>(smem + TILE * sizeof(int));
         const int MP = (t.M + 1) & ~1;
         int pe = -200;
-        for (int e = threadIdx.x; e < TILE_PAD * MP; e += CTA) {
+        for (int e = threadIdx.x; e < TILE_PAD * MP; e += NT) {
             const int i = e / MP, m = e - i * MP;
             float hi = 0.f, lo = 0.f;
             if (i < t.np && m < t.M) { hi = v.phi_hi[ph0 + (int64_t)i * t.M + m]; lo = v.phi_lo[ph0 + (int64_t)i * t.M + m]; }
@@ -687,7 +699,7 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
     } else {
         float4* s_phi = reinterpret_cast<float4*>(smem + TILE * sizeof(int));
         int pe = -200;
-        for (int e = threadIdx.x; e < TILE_PAD * t.M; e += CTA) {
+        for (int e = threadIdx.x; e < TILE_PAD * t.M; e += NT) {
             float hi = 0.f, lo = 0.f;
             if (e < t.np * t.M) { hi = v.phi_hi[ph0 + e]; lo = v.phi_lo[ph0 + e]; }
             s_phi[e] = make_float4(hi, hi, lo, lo);
@@ -699,10 +711,10 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
     unsigned char* s_gauge = smem + TILE * sizeof(int) + (size_t)TILE_PAD * v.maxM * (POL == P_F64 ? sizeof(double) : sizeof(float4));
     if (G) {
         if (POL == P_F64)
-            for (int i = threadIdx.x; i < TILE_PAD; i += CTA)
+            for (int i = threadIdx.x; i < TILE_PAD; i += NT)
                 reinterpret_cast<double2*>(s_gauge)[i] = (i < t.np) ? v.gauge_d[t.p0 + i] : make_double2(0.0, 0.0);
         else
-            for (int i = threadIdx.x; i < TILE_PAD; i += CTA)
+            for (int i = threadIdx.x; i < TILE_PAD; i += NT)
                 reinterpret_cast<float4*>(s_gauge)[i] = (i < t.np) ? v.gauge_f[t.p0 + i] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
@@ -724,15 +736,16 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
                 case 5: proj_body_pair2<5, Q, CH, PF>(v, t, ks, band, row, s_idx, s_phf, pe, poff); break;
                 default: proj_body_pair2<7, Q, CH, PF>(v, t, ks, band, row, s_idx, s_phf, pe, poff); break;
             }
-        } else if (POL == P_F32B2) {
+        } else if (POL == P_F32B2 || POL == P_F32B2F) {
+            constexpr int FOLD = (POL == P_F32B2F) ? 1 : 0;
             const float* s_phf = reinterpret_cast<const float*>(smem + TILE * sizeof(int));
             const float2* row0 = active ? reinterpret_cast<const float2*>(a.psi) + off : nullptr;
             const float2* row1 = (band + 1 < a.nbands) ? row0 + a.sn : nullptr;
             switch (t.M) {
-                case 1: proj_body_f32x2<1, Q, CH, PF>(v, t, ks, band, a.nbands, row0, row1, s_idx, s_phf, poff); break;
-                case 3: proj_body_f32x2<3, Q, CH, PF>(v, t, ks, band, a.nbands, row0, row1, s_idx, s_phf, poff); break;
-                case 5: proj_body_f32x2<5, Q, CH, PF>(v, t, ks, band, a.nbands, row0, row1, s_idx, s_phf, poff); break;
-                default: proj_body_f32x2<7, Q, CH, PF>(v, t, ks, band, a.nbands, row0, row1, s_idx, s_phf, poff); break;
+                case 1: proj_body_f32x2<1, Q, CH, PF, FOLD>(v, t, ks, band, a.nbands, row0, row1, s_idx, s_phf, poff); break;
+                case 3: proj_body_f32x2<3, Q, CH, PF, FOLD>(v, t, ks, band, a.nbands, row0, row1, s_idx, s_phf, poff); break;
+                case 5: proj_body_f32x2<5, Q, CH, PF, FOLD>(v, t, ks, band, a.nbands, row0, row1, s_idx, s_phf, poff); break;
+                default: proj_body_f32x2<7, Q, CH, PF, FOLD>(v, t, ks, band, a.nbands, row0, row1, s_idx, s_phf, poff); break;
             }
         } else if (POL == P_F64) {
             const double* s_phi = reinterpret_cast<const double*>(smem + TILE * sizeof(int));
@@ -771,23 +784,23 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
 
 // NDIR > 1: blockIdx.x = tile * NDIR + direction, so the CTAs of one tile and band chunk for the
 // NDIR orbital tables are neighbours in the launch and read the same states while they sit in L2.
-template <int POL, int Q, int CH, int NBG, int PF, int MINB, int G, int NDIR = 1>
-__global__ void __launch_bounds__(CTA, MINB) k_project(View v, ProjArgs a) {
+template <int POL, int Q, int CH, int NBG, int PF, int MINB, int G, int NDIR = 1, int NT = CTA>
+__global__ void __launch_bounds__(NT, MINB) k_project(View v, ProjArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_pe;
     const int tile = (NDIR == 1) ? (int)blockIdx.x : (int)blockIdx.x / NDIR;
     const int dir = (NDIR == 1) ? 0 : (int)blockIdx.x % NDIR;
-    project_item<POL, Q, CH, NBG, PF, G>(v, a, tile, blockIdx.z, blockIdx.y, smem, &s_pe, dir);
+    project_item<POL, Q, CH, NBG, PF, G, NT>(v, a, tile, blockIdx.z, blockIdx.y, smem, &s_pe, dir);
 }
 
 // Persistent form over many systems: every CTA takes (system, tile, k*spin) items from a counter until
 // the list is exhausted and processes all band chunks of the item's system.
-template <int POL, int Q, int CH, int NBG, int PF, int MINB>
-__global__ void __launch_bounds__(CTA, MINB) k_project_batch(const View* __restrict__ views, const ProjArgs* __restrict__ args,
+template <int POL, int Q, int CH, int NBG, int PF, int MINB, int NT = CTA>
+__global__ void __launch_bounds__(NT, MINB) k_project_batch(const View* __restrict__ views, const ProjArgs* __restrict__ args,
                                                           const int4* __restrict__ items, int nitems, int* counter) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_pe, s_item;
-    constexpr int BPC = (CTA / 32) * (32 / Q) * LaneBands<POL>::value;
+    constexpr int BPC = (NT / 32) * (32 / Q) * LaneBands<POL>::value;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
         __syncthreads();
@@ -798,7 +811,7 @@ __global__ void __launch_bounds__(CTA, MINB) k_project_batch(const View* __restr
         const ProjArgs& a = args[w.x];
         const int nchunks = (a.nbands + BPC * NBG - 1) / (BPC * NBG);
         for (int c = 0; c < nchunks; ++c) {
-            project_item<POL, Q, CH, NBG, PF, 0>(v, a, w.y, w.z, c, smem, &s_pe);
+            project_item<POL, Q, CH, NBG, PF, 0, NT>(v, a, w.y, w.z, c, smem, &s_pe);
             __syncthreads();   // the next chunk or item restages shared memory
         }
     }
@@ -871,40 +884,49 @@ __global__ void k_tile_reduce_batch(const View* __restrict__ views, const ProjAr
     tile_reduce_elem(views[blockIdx.y], args[blockIdx.y].nbands, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-template <int POL, int Q, int CH, int NBG, int PF, int MINB = 2, int G = 0, int NDIR = 1>
+template <int POL, int Q, int CH, int NBG, int PF, int MINB = 2, int G = 0, int NDIR = 1, int NT = CTA>
 static cudaError_t run_project(const View& v, const ProjArgs& a, cudaStream_t st) {
     static_assert(Q * CH <= TILE_PAD - TILE, "chained loops read up to Q*CH rows past the tile");
     size_t smem = TILE * sizeof(int) + (size_t)TILE_PAD * v.maxM * (POL == P_F64 ? sizeof(double) : sizeof(float4)) +
                   (G ? (size_t)TILE_PAD * 16 : 0);
-    auto fn = k_project<POL, Q, CH, NBG, PF, MINB, G, NDIR>;
+    auto fn = k_project<POL, Q, CH, NBG, PF, MINB, G, NDIR, NT>;
     cudaError_t e = cudaSuccess;
     if (!smem_configured((const void*)fn, (int)smem)) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    constexpr int BPC = (CTA / 32) * (32 / Q) * LaneBands<POL>::value;
+    constexpr int BPC = (NT / 32) * (32 / Q) * LaneBands<POL>::value;
     dim3 grid(v.ntiles * NDIR, (a.nbands + BPC * NBG - 1) / (BPC * NBG), v.nk * v.ns);
-    fn<<<grid, CTA, smem, st>>>(v, a);
+    fn<<<grid, NT, smem, st>>>(v, a);
     return cudaGetLastError();
+}
+
+// The default shape of a table row (variant 0): run_project with its thread count in the last place.
+template <int POL, int Q, int CH, int NBG, int PF, int MINB, int NT>
+static cudaError_t run_project_default(const View& v, const ProjArgs& a, cudaStream_t st) {
+    return run_project<POL, Q, CH, NBG, PF, MINB, 0, 1, NT>(v, a, st);
 }
 
 // The shapes selectable with dftu_set_kernel_variant, listed once for the single-system and the batched
 // launches: X(variant, policy, lanes per band Q, points per chain, band groups per CTA, L2 prefetch,
-// minimum blocks per SM).  Variant 0 is the default case of each switch.  P_PAIR2 is the FP32-pair
-// arithmetic with paired orbitals, P_F32B2 the complex64 form with two bands per lane.
+// minimum blocks per SM, threads per CTA).  Variant 0 is the default case of each switch.  P_PAIR2 is
+// the FP32-pair arithmetic with paired orbitals, P_F32B2 the complex64 form with two bands per lane,
+// P_F32B2F the same with each product's hi and lo halves folded into one sum.
 #define DFTU_PROJECT_SHAPES_F32(X) \
-    X(1, P_F32, 8, 16, 8, 0, 2) X(2, P_F32B2, 8, 8, 2, 0, 2) X(3, P_F32B2, 8, 8, 8, 0, 2) X(4, P_F32B2, 4, 16, 2, 0, 2) \
-    X(5, P_F32B2, 16, 8, 4, 0, 2) X(6, P_F32B2, 8, 8, 4, 2, 2) X(7, P_F32B2, 16, 8, 4, 2, 2)
-#define DFTU_PROJECT_DEFAULT_F32 P_F32B2, 8, 8, 4, 0, 2
+    X(1, P_F32, 8, 16, 8, 0, 2, 256) X(2, P_F32B2F, 8, 8, 4, 0, 3, 256) X(3, P_F32B2, 8, 8, 4, 0, 2, 256) \
+    X(4, P_F32B2F, 16, 8, 4, 0, 2, 256) X(5, P_F32B2F, 16, 8, 8, 0, 3, 256) X(6, P_F32B2F, 16, 6, 4, 0, 3, 256) \
+    X(7, P_F32B2F, 8, 12, 4, 0, 2, 256)
+#define DFTU_PROJECT_DEFAULT_F32 P_F32B2F, 16, 8, 4, 0, 3, 256
 #define DFTU_PROJECT_SHAPES_PAIR(X) \
-    X(1, P_PAIR, 4, 8, 4, 1, 2) X(2, P_PAIR, 4, 8, 4, 0, 2) X(3, P_PAIR2, 4, 8, 8, 1, 2) X(4, P_PAIR, 4, 8, 8, 2, 2) \
-    X(5, P_PAIR, 8, 8, 4, 1, 2) X(6, P_PAIR, 8, 8, 4, 2, 2) X(7, P_PAIR, 8, 16, 4, 1, 2)
-#define DFTU_PROJECT_DEFAULT_PAIR P_PAIR, 4, 8, 8, 1, 2
+    X(1, P_PAIR, 4, 8, 4, 1, 2, 256) X(2, P_PAIR, 4, 8, 4, 0, 2, 256) X(3, P_PAIR2, 4, 8, 8, 1, 2, 256) \
+    X(4, P_PAIR, 4, 8, 16, 1, 2, 256) X(5, P_PAIR, 8, 8, 4, 1, 2, 256) X(6, P_PAIR, 8, 8, 8, 1, 2, 256) \
+    X(7, P_PAIR, 8, 16, 4, 1, 2, 256)
+#define DFTU_PROJECT_DEFAULT_PAIR P_PAIR, 4, 8, 8, 1, 2, 256
 
 cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_f64_mode mode, int nbands,
                            int64_t sk, int64_t ss, int64_t sn, int variant, cudaStream_t st, bool gauge) {
     ProjArgs a{psi, sk, ss, sn, nbands};
     cudaError_t e;
-#define DFTU_CASE_F32(i, POL, Q, CH, NBG, PF, MB) case i: e = run_project<POL, Q, CH, NBG, PF, MB>(v, a, st); break;
-#define DFTU_CASE_PAIR(i, POL, Q, CH, NBG, PF, MB) case i: e = run_project<POL, Q, CH, NBG, PF, MB>(v, a, st); break;
+#define DFTU_CASE_F32(i, POL, Q, CH, NBG, PF, MB, NT) case i: e = run_project<POL, Q, CH, NBG, PF, MB, 0, 1, NT>(v, a, st); break;
+#define DFTU_CASE_PAIR(i, POL, Q, CH, NBG, PF, MB, NT) case i: e = run_project<POL, Q, CH, NBG, PF, MB, 0, 1, NT>(v, a, st); break;
     if (gauge) {   // one shape per arithmetic policy with the gauge phases (Sec. V)
         if (prec == DFTU_C64) e = run_project<P_F32, 8, 16, 8, 0, 2, 1>(v, a, st);
         else if (mode == DFTU_F64_NATIVE) e = run_project<P_F64, 8, 1, 4, 0, 2, 1>(v, a, st);
@@ -912,14 +934,14 @@ cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_
     } else if (prec == DFTU_C64) {
         switch (variant) {
             DFTU_PROJECT_SHAPES_F32(DFTU_CASE_F32)
-            default: e = run_project<DFTU_PROJECT_DEFAULT_F32>(v, a, st); break;
+            default: e = run_project_default<DFTU_PROJECT_DEFAULT_F32>(v, a, st); break;
         }
     } else if (mode == DFTU_F64_NATIVE) {
         e = run_project<P_F64, 8, 1, 4, 0>(v, a, st);
     } else {
         switch (variant) {
             DFTU_PROJECT_SHAPES_PAIR(DFTU_CASE_PAIR)
-            default: e = run_project<DFTU_PROJECT_DEFAULT_PAIR>(v, a, st); break;
+            default: e = run_project_default<DFTU_PROJECT_DEFAULT_PAIR>(v, a, st); break;
         }
     }
 #undef DFTU_CASE_F32
@@ -952,29 +974,29 @@ cudaError_t launch_project_dirs(const View& v, const void* psi, dftu_prec prec, 
     return cudaSuccess;
 }
 
-template <int POL, int Q, int CH, int NBG, int PF, int MINB = 2>
+template <int POL, int Q, int CH, int NBG, int PF, int MINB = 2, int NT = CTA>
 static cudaError_t run_project_batch(const BatchLaunch& b, cudaStream_t st) {
     size_t smem = TILE * sizeof(int) + (size_t)TILE_PAD * b.maxM * (POL == P_F64 ? sizeof(double) : sizeof(float4));
     cudaError_t e = cudaSuccess;
-    auto fn = k_project_batch<POL, Q, CH, NBG, PF, MINB>;
+    auto fn = k_project_batch<POL, Q, CH, NBG, PF, MINB, NT>;
     if (!smem_configured((const void*)fn, (int)smem)) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0, nsm = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, CTA, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, smem);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(b.counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     int grid = std::max(1, std::min(per_sm * nsm, b.nitems));
-    fn<<<grid, CTA, smem, st>>>(b.views, b.args, b.items, b.nitems, b.counter);
+    fn<<<grid, NT, smem, st>>>(b.views, b.args, b.items, b.nitems, b.counter);
     return cudaGetLastError();
 }
 
 cudaError_t launch_project_batch(const BatchLaunch& b, dftu_prec prec, dftu_f64_mode mode, int variant, cudaStream_t st) {
     cudaError_t e;
-#define DFTU_CASE_F32(i, POL, Q, CH, NBG, PF, MB) case i: e = run_project_batch<POL, Q, CH, NBG, PF, MB>(b, st); break;
-#define DFTU_CASE_PAIR(i, POL, Q, CH, NBG, PF, MB) case i: e = run_project_batch<POL, Q, CH, NBG, PF, MB>(b, st); break;
+#define DFTU_CASE_F32(i, POL, Q, CH, NBG, PF, MB, NT) case i: e = run_project_batch<POL, Q, CH, NBG, PF, MB, NT>(b, st); break;
+#define DFTU_CASE_PAIR(i, POL, Q, CH, NBG, PF, MB, NT) case i: e = run_project_batch<POL, Q, CH, NBG, PF, MB, NT>(b, st); break;
     if (prec == DFTU_C64) {
         switch (variant) {
             DFTU_PROJECT_SHAPES_F32(DFTU_CASE_F32)
