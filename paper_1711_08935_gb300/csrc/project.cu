@@ -10,8 +10,8 @@
 //
 // Arithmetic policies
 //   F64  : complex128 states, FP64 FMAs (the FP64 pipe of this GPU runs at ~1/70 of FP32).
-//   PAIR : complex128 states carried as pairs of FP32 numbers.  Each double is split exactly
-//          (integer ops) into hi + lo floats scaled by 2^-Emax of its chain; products accumulate
+//   PAIR : complex128 states carried as pairs of FP32 numbers.  Each double is split (integer ops,
+//          47 significant bits) into hi + lo floats scaled by 2^-Emax of its chain; products accumulate
 //          into an accumulator offset by a power of two C >= 4*sum|terms| so that the running sum
 //          moves in one binade: t = s - acc is exact and the rounding residual a*b - t is caught
 //          in a second float.  Chains are merged with TwoSum.  Accuracy ~2^-44 of the chain scale.
@@ -242,22 +242,26 @@ __device__ __forceinline__ void proj_body_f32(const View& v, const Tile& t, int 
 // ------------------------------------------------------------------------------------------------
 // PAIR policy (complex128 states, FP32-pair arithmetic)
 // ------------------------------------------------------------------------------------------------
-// Split a double with biased exponent field E <= Em (Em >= 127) into floats hi + lo of x * 2^(1023-Em):
-// hi = the top 24 significant bits, lo = the next 23 (error < 2^-46 of 2^(E-Em)).  Both are formed
-// as an exact float mantissa times the signed power of two 2^(E-Em): hi from the top 23 fraction bits
-// under exponent 127, lo from the next 23 bits as (1.f - 1) 2^-23.  Values 2^126 below 2^(Em-1023),
-// zeros and denormals give hi = lo = 0 (Em >= 127 makes the scale of E = 0 vanish).
-__device__ __forceinline__ void split_scaled(double x, int Em, float& hi, float& lo) {
+// Split a double x with biased exponent field E <= Em (Em >= 127, the chain's largest) into floats
+// hi + lo of x * 2^(1023-Em) by assembling their bit patterns with integer operations: hi takes the
+// sign, the exponent E - Em + 127 and the top 23 fraction bits (a funnel shift of the two words after
+// the exponent is rebased in place); lo the next 23 fraction bits under the exponent of hi less 23,
+// minus the implicit one of that pattern (an exact subtraction).  47 significant bits, error below
+// 2^-46 of 2^(E-Em).  bias = (Em - 127) << 20.  Magnitudes more than 2^103 below 2^(Em-1023), zeros
+// included, are raised to that floor (an absolute change below 2^-102 of the chain scale), so both
+// exponents stay normal without a branch.
+__device__ __forceinline__ void split_bits(double x, int bias, float& hi, float& lo) {
     const unsigned whi = (unsigned)__double2hiint(x), wlo = (unsigned)__double2loint(x);
-    const unsigned mh = (__funnelshift_l(wlo, whi, 3) & 0x007FFFFFu) | 0x3F800000u;   // 1.f, top 23 fraction bits
-    const unsigned ml = ((wlo >> 6) & 0x007FFFFFu) | 0x3F800000u;                     // 1.g, next 23 bits
-    const int eh = max((int)((whi >> 20) & 0x7FFu) + 127 - Em, 0);                    // exponent of 2^(E-Em)
-    const float sc = __uint_as_float(((unsigned)eh << 23) + (whi & 0x80000000u));   // signed scale, 0 below range
-    hi = __uint_as_float(mh) * sc;
-    lo = __fmaf_rn(__uint_as_float(ml), 0x1p-23f, -0x1p-23f) * sc;
+    const int a = max((int)(whi & 0x7FFFFFFFu) - bias, 24 << 20);                 // exponent field E' >= 24
+    const unsigned hb = __funnelshift_l(wlo, (unsigned)a, 3) | (whi & 0x80000000u);
+    const unsigned one = (hb - (23u << 23)) & 0xFF800000u;                         // +-2^(E' - 150)
+    hi = __uint_as_float(hb);
+    lo = __uint_as_float(one | ((wlo >> 6) & 0x007FFFFFu)) - __uint_as_float(one);
 }
 
-__device__ __forceinline__ int exp_field(double x) { return (__double2hiint(x) >> 20) & 0x7FF; }
+// the exponent field of x in place (a mask other than the split's, so the compiler does not keep one
+// shared masked word per point alive across the chain)
+__device__ __forceinline__ unsigned exp_bits(double x) { return (unsigned)__double2hiint(x) & 0x7FF00000u; }
 
 // (bh + bl) * (g.x + g.z + i (g.y + g.w)) as a new float pair, componentwise for (re, im): the hi
 // products are formed exactly (product + FMA residual) and added with TwoSum, the cross terms with
@@ -282,9 +286,81 @@ __device__ __forceinline__ void rot_pair(float2& bh, float2& bl, float4 g) {
     bl = lo;
 }
 
+// The Q*CH-point chain starting at i0 (lane points i0 + c*Q) into registers, zeros past the tile.
+template <int Q, int CH>
+__device__ __forceinline__ void pair_load(double2 (&x)[CH], int i0, const double2* __restrict__ row, const int* s_idx, int np) {
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        int i = i0 + c * Q;
+        x[c] = (i < np) ? __ldg(row + s_idx[i]) : make_double2(0.0, 0.0);
+    }
+}
+
+// One chain of the FP32-pair projection: the chain's scale (Em_run rises to its largest exponent and R
+// is rescaled), the split states, the offset-accumulated products, merged into R.
+template <int M, int Q, int CH, int G>
+__device__ __forceinline__ void pair_chain(const double2 (&x)[CH], int i0, DF2 (&R)[M], int& Em_run, bool& bad, float Cv,
+                                           const float4* s_phi, const float4* s_g) {
+    const float2 C2 = make_float2(Cv, Cv);
+    const float2 mone = make_float2(-1.f, -1.f);
+    unsigned am = 0;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) am = max(am, max(exp_bits(x[c].x), exp_bits(x[c].y)));
+    int Ec = (int)(am >> 20);
+    if (Ec == 0x7FF) bad = true;
+    if (Ec == 0) return;
+    Ec = max(Ec, 127);   // the split needs Em >= 127 (zeros then scale to 0)
+    if (Ec > Em_run) {
+        if (Em_run != 0) {
+            float s = pow2f(Em_run - Ec);
+            float2 s2 = make_float2(s, s);
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                R[m].h = __fmul2_rn(R[m].h, s2);
+                R[m].l = __fmul2_rn(R[m].l, s2);
+            }
+        }
+        Em_run = Ec;
+    }
+    float2 acc[M], lo[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) { acc[m] = C2; lo[m] = make_float2(0.f, 0.f); }
+    const int bias = (Em_run - 127) << 20;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        float2 bh, bl;
+        split_bits(x[c].x, bias, bh.x, bl.x);
+        split_bits(x[c].y, bias, bh.y, bl.y);
+        if (G) rot_pair(bh, bl, s_g[i0 + c * Q]);
+        const float4* ph = s_phi + (i0 + c * Q) * M;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            float4 f = ph[m];                                  // (hi, hi, lo, lo)
+            float2 ah = make_float2(f.x, f.y), al = make_float2(f.z, f.w);
+            float2 s = ffma2(ah, bh, acc[m]);                  // acc + a*b, rounded
+            float2 tneg = ffma2(s, mone, acc[m]);              // acc - s  (exact: same binade)
+            float2 r = ffma2(ah, bh, tneg);                    // rounding residual a*b - (s - acc)
+            lo[m] = fadd2(lo[m], r);
+            lo[m] = ffma2(ah, bl, lo[m]);
+            lo[m] = ffma2(al, bh, lo[m]);
+            acc[m] = s;
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        DF2 chn{fadd2(acc[m], make_float2(-Cv, -Cv)), lo[m]};  // exact removal of the offset
+        df_add(R[m], chn);
+    }
+}
+
+// Each lane takes chains of CH points (i0 + c*Q), one after another, and merges each into R.
+// PF = 1: every chain asks L2 for the next one; PF = 5: in addition the last chain of the tile asks for
+// the first chain of the band the lane takes next (row_next, null if none), so only the first band
+// group of a CTA starts cold.
 template <int M, int Q, int CH, int PF, int G>
 __device__ __forceinline__ void proj_body_pair(const View& v, const Tile& t, int ks, int band, const double2* __restrict__ row,
-                                               const int* s_idx, const float4* s_phi, int pe, const float4* s_g, int64_t poff) {
+                                               const double2* __restrict__ row_next, const int* s_idx, const float4* s_phi,
+                                               int pe, const float4* s_g, int64_t poff) {
     const int q = threadIdx.x & (Q - 1);
     DF2 R[M];
 #pragma unroll
@@ -295,71 +371,36 @@ __device__ __forceinline__ void proj_body_pair(const View& v, const Tile& t, int
     // (one more power of two when x' is rotated by a gauge phase: |x'| < 2 sqrt 2)
     constexpr int LOG2CH = (CH >= 16) ? 4 : (CH >= 8) ? 3 : (CH >= 4) ? 2 : (CH >= 2) ? 1 : 0;
     const float Cv = pow2f(min(max(pe + 3 + G + LOG2CH, -100), 100));
-    const float2 C2 = make_float2(Cv, Cv);
-    const float2 mone = make_float2(-1.f, -1.f);
-    if (row) {
-        for (int i0 = q; i0 < t.np; i0 += Q * CH) {
-            double2 x[CH];
+#define DFTU_PAIR_CHAIN(x, i0) pair_chain<M, Q, CH, G>(x, i0, R, Em_run, bad, Cv, s_phi, s_g)
+#define DFTU_PAIR_LOAD(x, i0) pair_load<Q, CH>(x, i0, row, s_idx, t.np)
+    // L2 prefetch of the chain starting at i0; past the tile (PF == 5) the first chain of the next band
+    auto prefetch = [&](int i0) {
+        if (PF == 1 || PF == 5 || (PF == 2 && (q == 0 || q == Q - 1))) {   // PF == 2: the group's edge lanes only
+            if (PF == 5 && i0 >= t.np) {
+                if (row_next)
 #pragma unroll
-            for (int c = 0; c < CH; ++c) {
-                int i = i0 + c * Q;
-                x[c] = (i < t.np) ? __ldg(row + s_idx[i]) : make_double2(0.0, 0.0);
-            }
-            if (PF == 1 || (PF == 2 && (q == 0 || q == Q - 1))) {   // PF == 2: the group's edge lanes only
+                    for (int c = 0; c < CH; ++c) {
+                        int i = q + c * Q;
+                        if (i < t.np) prefetch_l2(row_next + s_idx[i]);
+                    }
+            } else {
 #pragma unroll
                 for (int c = 0; c < CH; ++c) {
-                    int i = i0 + Q * CH + c * Q;
+                    int i = i0 + c * Q;
                     if (i < t.np) prefetch_l2(row + s_idx[i]);
                 }
             }
-            int Ec = 0;
-#pragma unroll
-            for (int c = 0; c < CH; ++c) Ec = max(Ec, max(exp_field(x[c].x), exp_field(x[c].y)));
-            if (Ec == 0x7FF) bad = true;
-            if (Ec == 0) continue;
-            Ec = max(Ec, 127);   // the split needs Em >= 127 (zeros then scale to 0)
-            if (Ec > Em_run) {
-                if (Em_run != 0) {
-                    float s = pow2f(Em_run - Ec);
-                    float2 s2 = make_float2(s, s);
-#pragma unroll
-                    for (int m = 0; m < M; ++m) {
-                        R[m].h = __fmul2_rn(R[m].h, s2);
-                        R[m].l = __fmul2_rn(R[m].l, s2);
-                    }
-                }
-                Em_run = Ec;
-            }
-            float2 acc[M], lo[M];
-#pragma unroll
-            for (int m = 0; m < M; ++m) { acc[m] = C2; lo[m] = make_float2(0.f, 0.f); }
-#pragma unroll
-            for (int c = 0; c < CH; ++c) {
-                float2 bh, bl;
-                split_scaled(x[c].x, Em_run, bh.x, bl.x);
-                split_scaled(x[c].y, Em_run, bh.y, bl.y);
-                if (G) rot_pair(bh, bl, s_g[i0 + c * Q]);
-                const float4* ph = s_phi + (i0 + c * Q) * M;
-#pragma unroll
-                for (int m = 0; m < M; ++m) {
-                    float4 f = ph[m];                                  // (hi, hi, lo, lo)
-                    float2 ah = make_float2(f.x, f.y), al = make_float2(f.z, f.w);
-                    float2 s = ffma2(ah, bh, acc[m]);                  // acc + a*b, rounded
-                    float2 tneg = ffma2(s, mone, acc[m]);              // acc - s  (exact: same binade)
-                    float2 r = ffma2(ah, bh, tneg);                    // rounding residual a*b - (s - acc)
-                    lo[m] = fadd2(lo[m], r);
-                    lo[m] = ffma2(ah, bl, lo[m]);
-                    lo[m] = ffma2(al, bh, lo[m]);
-                    acc[m] = s;
-                }
-            }
-#pragma unroll
-            for (int m = 0; m < M; ++m) {
-                DF2 chn{fadd2(acc[m], make_float2(-Cv, -Cv)), lo[m]};  // exact removal of the offset
-                df_add(R[m], chn);
-            }
         }
-    }
+    };
+    if (row)
+        for (int i0 = q; i0 < t.np; i0 += Q * CH) {
+            double2 x[CH];
+            DFTU_PAIR_LOAD(x, i0);
+            prefetch(i0 + Q * CH);
+            DFTU_PAIR_CHAIN(x, i0);
+        }
+#undef DFTU_PAIR_CHAIN
+#undef DFTU_PAIR_LOAD
     // bring the Q lanes of this band to a common scale, then add in pairs
     int Em_max = Em_run;
 #pragma unroll
@@ -393,150 +434,6 @@ __device__ __forceinline__ void proj_body_pair(const View& v, const Tile& t, int
                 if (m == mq) a = R[m];
             double re = f2d_scaled(a.h.x, sc) + f2d_scaled(a.l.x, sc);
             double im = f2d_scaled(a.h.y, sc) + f2d_scaled(a.l.y, sc);
-            if (anybad) { re = __longlong_as_double(0x7FF8000000000000LL); im = re; }
-            write_partial(v, t, ks, band, mq, re, im, poff);
-        });
-    }
-}
-
-// ------------------------------------------------------------------------------------------------
-// PAIR policy with paired orbitals (complex128 states)
-// ------------------------------------------------------------------------------------------------
-// The arithmetic of proj_body_pair (split states, offset accumulator, residual in a second float),
-// with the shared-memory rows of the F32 policy: per point [hi_0 .. hi_{MP-1}, lo_0 .. lo_{MP-1}].
-// Two orbitals share one 8-byte shared load and every f32x2 instruction, against a broadcast state
-// component, so a point costs MP/2 hi and MP/2 lo loads instead of M 16-byte (hi, hi, lo, lo) loads.
-template <int M, int Q, int CH, int PF>
-__device__ __forceinline__ void proj_body_pair2(const View& v, const Tile& t, int ks, int band, const double2* __restrict__ row,
-                                                const int* s_idx, const float* s_phf, int pe, int64_t poff) {
-    constexpr int MP = (M + 1) & ~1, NP = MP / 2;
-    const int q = threadIdx.x & (Q - 1);
-    DF2 Rr[NP], Ri[NP];   // running sums of the real and imaginary parts, orbitals (2j, 2j+1)
-#pragma unroll
-    for (int j = 0; j < NP; ++j) {
-        Rr[j] = DF2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-        Ri[j] = Rr[j];
-    }
-    int Em_run = 0;
-    bool bad = false;
-    constexpr int LOG2CH = (CH >= 16) ? 4 : (CH >= 8) ? 3 : (CH >= 4) ? 2 : (CH >= 2) ? 1 : 0;
-    const float Cv = pow2f(min(max(pe + 3 + LOG2CH, -100), 100));   // >= 4 * CH * max|phi x'|, |x'| < 2
-    const float2 C2 = make_float2(Cv, Cv);
-    const float2 mone = make_float2(-1.f, -1.f);
-    if (row) {
-        for (int i0 = q; i0 < t.np; i0 += Q * CH) {
-            double2 x[CH];
-#pragma unroll
-            for (int c = 0; c < CH; ++c) {
-                int i = i0 + c * Q;
-                x[c] = (i < t.np) ? __ldg(row + s_idx[i]) : make_double2(0.0, 0.0);
-            }
-            if (PF == 1 || (PF == 2 && (q == 0 || q == Q - 1))) {   // PF == 2: the group's edge lanes only
-#pragma unroll
-                for (int c = 0; c < CH; ++c) {
-                    int i = i0 + Q * CH + c * Q;
-                    if (i < t.np) prefetch_l2(row + s_idx[i]);
-                }
-            }
-            int Ec = 0;
-#pragma unroll
-            for (int c = 0; c < CH; ++c) Ec = max(Ec, max(exp_field(x[c].x), exp_field(x[c].y)));
-            if (Ec == 0x7FF) bad = true;
-            if (Ec == 0) continue;
-            Ec = max(Ec, 127);
-            if (Ec > Em_run) {
-                if (Em_run != 0) {
-                    const float sc = pow2f(Em_run - Ec);
-                    const float2 s2 = make_float2(sc, sc);
-#pragma unroll
-                    for (int j = 0; j < NP; ++j) {
-                        Rr[j].h = __fmul2_rn(Rr[j].h, s2); Rr[j].l = __fmul2_rn(Rr[j].l, s2);
-                        Ri[j].h = __fmul2_rn(Ri[j].h, s2); Ri[j].l = __fmul2_rn(Ri[j].l, s2);
-                    }
-                }
-                Em_run = Ec;
-            }
-            float2 aR[NP], lR[NP], aI[NP], lI[NP];
-#pragma unroll
-            for (int j = 0; j < NP; ++j) {
-                aR[j] = C2; aI[j] = C2;
-                lR[j] = make_float2(0.f, 0.f); lI[j] = lR[j];
-            }
-#pragma unroll
-            for (int c = 0; c < CH; ++c) {
-                float rh, rl, ih, il;
-                split_scaled(x[c].x, Em_run, rh, rl);
-                split_scaled(x[c].y, Em_run, ih, il);
-                const float2 brh = make_float2(rh, rh), brl = make_float2(rl, rl);
-                const float2 bih = make_float2(ih, ih), bil = make_float2(il, il);
-                const float* ph = s_phf + (i0 + c * Q) * (2 * MP);
-#pragma unroll
-                for (int j = 0; j < NP; ++j) {
-                    const float2 ah = *reinterpret_cast<const float2*>(ph + 2 * j);
-                    const float2 al = *reinterpret_cast<const float2*>(ph + MP + 2 * j);
-                    float2 sr = ffma2(ah, brh, aR[j]);
-                    float2 tr = ffma2(sr, mone, aR[j]);                // aR - sr, exact
-                    lR[j] = fadd2(lR[j], ffma2(ah, brh, tr));           // rounding residual
-                    lR[j] = ffma2(ah, brl, lR[j]);
-                    lR[j] = ffma2(al, brh, lR[j]);
-                    aR[j] = sr;
-                    float2 si = ffma2(ah, bih, aI[j]);
-                    float2 ti = ffma2(si, mone, aI[j]);
-                    lI[j] = fadd2(lI[j], ffma2(ah, bih, ti));
-                    lI[j] = ffma2(ah, bil, lI[j]);
-                    lI[j] = ffma2(al, bih, lI[j]);
-                    aI[j] = si;
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < NP; ++j) {
-                df_add(Rr[j], DF2{fadd2(aR[j], make_float2(-Cv, -Cv)), lR[j]});
-                df_add(Ri[j], DF2{fadd2(aI[j], make_float2(-Cv, -Cv)), lI[j]});
-            }
-        }
-    }
-    int Em_max = Em_run;
-#pragma unroll
-    for (int off = Q / 2; off > 0; off >>= 1) Em_max = max(Em_max, __shfl_xor_sync(0xffffffffu, Em_max, off));
-    if (Em_run != Em_max) {
-        const float sc = (Em_run == 0) ? 0.0f : pow2f(Em_run - Em_max);
-        const float2 s2 = make_float2(sc, sc);
-#pragma unroll
-        for (int j = 0; j < NP; ++j) {
-            Rr[j].h = __fmul2_rn(Rr[j].h, s2); Rr[j].l = __fmul2_rn(Rr[j].l, s2);
-            Ri[j].h = __fmul2_rn(Ri[j].h, s2); Ri[j].l = __fmul2_rn(Ri[j].l, s2);
-        }
-    }
-#pragma unroll
-    for (int off = Q / 2; off > 0; off >>= 1)
-#pragma unroll
-        for (int j = 0; j < NP; ++j) {
-            DF2 o{make_float2(shfl_x(Rr[j].h.x, off), shfl_x(Rr[j].h.y, off)),
-                  make_float2(shfl_x(Rr[j].l.x, off), shfl_x(Rr[j].l.y, off))};
-            df_add(Rr[j], o);
-            DF2 u{make_float2(shfl_x(Ri[j].h.x, off), shfl_x(Ri[j].h.y, off)),
-                  make_float2(shfl_x(Ri[j].l.x, off), shfl_x(Ri[j].l.y, off))};
-            df_add(Ri[j], u);
-        }
-    int anybad = bad ? 1 : 0;
-#pragma unroll
-    for (int off = Q / 2; off > 0; off >>= 1) anybad |= __shfl_xor_sync(0xffffffffu, anybad, off);
-    if (row) {
-        const int sc = Em_max - 1023;
-        per_lane_orbital<M, Q>(q, [&](int mq) {
-            float rh = Rr[0].h.x, rl = Rr[0].l.x, ih = Ri[0].h.x, il = Ri[0].l.x;
-#pragma unroll
-            for (int m = 1; m < M; ++m)
-                if (m == mq) {
-                    const DF2& a = Rr[m / 2];
-                    const DF2& b = Ri[m / 2];
-                    rh = (m & 1) ? a.h.y : a.h.x;
-                    rl = (m & 1) ? a.l.y : a.l.x;
-                    ih = (m & 1) ? b.h.y : b.h.x;
-                    il = (m & 1) ? b.l.y : b.l.x;
-                }
-            double re = f2d_scaled(rh, sc) + f2d_scaled(rl, sc);
-            double im = f2d_scaled(ih, sc) + f2d_scaled(il, sc);
             if (anybad) { re = __longlong_as_double(0x7FF8000000000000LL); im = re; }
             write_partial(v, t, ks, band, mq, re, im, poff);
         });
@@ -655,7 +552,7 @@ __device__ __forceinline__ void proj_body_f32x2(const View& v, const Tile& t, in
 // ------------------------------------------------------------------------------------------------
 // kernels
 // ------------------------------------------------------------------------------------------------
-enum Pol { P_F64 = 0, P_PAIR = 1, P_F32 = 2, P_PAIR2 = 3, P_F32B2 = 4, P_F32B2F = 5 };
+enum Pol { P_F64 = 0, P_PAIR = 1, P_F32 = 2, P_F32B2 = 4, P_F32B2F = 5 };
 
 // bands a lane carries at once
 template <int POL> struct LaneBands { static constexpr int value = (POL == P_F32B2 || POL == P_F32B2F) ? 2 : 1; };
@@ -683,7 +580,7 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
         double* s_phi = reinterpret_cast<double*>(smem + TILE * sizeof(int));
         for (int e = threadIdx.x; e < TILE * t.M; e += NT)
             s_phi[e] = (e < t.np * t.M) ? v.phi64[ph0 + e] : 0.0;
-    } else if (POL == P_F32 || POL == P_PAIR2 || POL == P_F32B2 || POL == P_F32B2F) {
+    } else if (POL == P_F32 || POL == P_F32B2 || POL == P_F32B2F) {
         float* s_phf = reinterpret_cast<float*>(smem + TILE * sizeof(int));
         const int MP = (t.M + 1) & ~1;
         int pe = -200;
@@ -695,7 +592,6 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
             s_phf[i * 2 * MP + MP + m] = lo;
             if (hi != 0.f) pe = max(pe, ((__float_as_int(hi) >> 23) & 0xFF) - 127 + 1);   // |hi| < 2^pe
         }
-        if (POL == P_PAIR2) atomicMax(s_pe, pe);
     } else {
         float4* s_phi = reinterpret_cast<float4*>(smem + TILE * sizeof(int));
         int pe = -200;
@@ -726,17 +622,7 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
         const int band = band0 + (threadIdx.x >> 5) * BPW + ((threadIdx.x & 31) / Q) * NBL;
         const bool active = band < a.nbands;
         const int64_t off = (int64_t)k * a.sk + (int64_t)s * a.ss + (int64_t)band * a.sn;
-        if (POL == P_PAIR2) {
-            const float* s_phf = reinterpret_cast<const float*>(smem + TILE * sizeof(int));
-            const double2* row = active ? reinterpret_cast<const double2*>(a.psi) + off : nullptr;
-            const int pe = *s_pe;
-            switch (t.M) {
-                case 1: proj_body_pair2<1, Q, CH, PF>(v, t, ks, band, row, s_idx, s_phf, pe, poff); break;
-                case 3: proj_body_pair2<3, Q, CH, PF>(v, t, ks, band, row, s_idx, s_phf, pe, poff); break;
-                case 5: proj_body_pair2<5, Q, CH, PF>(v, t, ks, band, row, s_idx, s_phf, pe, poff); break;
-                default: proj_body_pair2<7, Q, CH, PF>(v, t, ks, band, row, s_idx, s_phf, pe, poff); break;
-            }
-        } else if (POL == P_F32B2 || POL == P_F32B2F) {
+        if (POL == P_F32B2 || POL == P_F32B2F) {
             constexpr int FOLD = (POL == P_F32B2F) ? 1 : 0;
             const float* s_phf = reinterpret_cast<const float*>(smem + TILE * sizeof(int));
             const float2* row0 = active ? reinterpret_cast<const float2*>(a.psi) + off : nullptr;
@@ -760,13 +646,14 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
         } else if (POL == P_PAIR) {
             const float4* s_phi = reinterpret_cast<const float4*>(smem + TILE * sizeof(int));
             const double2* row = active ? reinterpret_cast<const double2*>(a.psi) + off : nullptr;
+            const double2* row_next = (active && g + 1 < NBG && band + BPC < a.nbands) ? row + (int64_t)BPC * a.sn : nullptr;
             const int pe = *s_pe;
             const float4* s_g = reinterpret_cast<const float4*>(s_gauge);
             switch (t.M) {
-                case 1: proj_body_pair<1, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phi, pe, s_g, poff); break;
-                case 3: proj_body_pair<3, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phi, pe, s_g, poff); break;
-                case 5: proj_body_pair<5, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phi, pe, s_g, poff); break;
-                default: proj_body_pair<7, Q, CH, PF, G>(v, t, ks, band, row, s_idx, s_phi, pe, s_g, poff); break;
+                case 1: proj_body_pair<1, Q, CH, PF, G>(v, t, ks, band, row, row_next, s_idx, s_phi, pe, s_g, poff); break;
+                case 3: proj_body_pair<3, Q, CH, PF, G>(v, t, ks, band, row, row_next, s_idx, s_phi, pe, s_g, poff); break;
+                case 5: proj_body_pair<5, Q, CH, PF, G>(v, t, ks, band, row, row_next, s_idx, s_phi, pe, s_g, poff); break;
+                default: proj_body_pair<7, Q, CH, PF, G>(v, t, ks, band, row, row_next, s_idx, s_phi, pe, s_g, poff); break;
             }
         } else {
             const float* s_phf = reinterpret_cast<const float*>(smem + TILE * sizeof(int));
@@ -907,19 +794,20 @@ static cudaError_t run_project_default(const View& v, const ProjArgs& a, cudaStr
 
 // The shapes selectable with dftu_set_kernel_variant, listed once for the single-system and the batched
 // launches: X(variant, policy, lanes per band Q, points per chain, band groups per CTA, L2 prefetch,
-// minimum blocks per SM, threads per CTA).  Variant 0 is the default case of each switch.  P_PAIR2 is
-// the FP32-pair arithmetic with paired orbitals, P_F32B2 the complex64 form with two bands per lane,
-// P_F32B2F the same with each product's hi and lo halves folded into one sum.
+// minimum blocks per SM, threads per CTA).  Variant 0 is the default case of each switch.  P_F32B2 is
+// the complex64 form with two bands per lane, P_F32B2F the same with each product's hi and lo halves
+// folded into one sum, P_F32 one band per lane.  PAIR L2 prefetch: 1 = the next chain, 5 = also the
+// next band's first chain.
 #define DFTU_PROJECT_SHAPES_F32(X) \
-    X(1, P_F32, 8, 16, 8, 0, 2, 256) X(2, P_F32B2F, 8, 8, 4, 0, 3, 256) X(3, P_F32B2, 8, 8, 4, 0, 2, 256) \
+    X(1, P_F32B2F, 16, 8, 4, 1, 3, 256) X(2, P_F32B2F, 8, 8, 4, 0, 3, 256) X(3, P_F32B2, 8, 8, 4, 0, 2, 256) \
     X(4, P_F32B2F, 16, 8, 4, 0, 2, 256) X(5, P_F32B2F, 16, 8, 8, 0, 3, 256) X(6, P_F32B2F, 16, 6, 4, 0, 3, 256) \
-    X(7, P_F32B2F, 8, 12, 4, 0, 2, 256)
+    X(7, P_F32, 8, 16, 8, 0, 2, 256)
 #define DFTU_PROJECT_DEFAULT_F32 P_F32B2F, 16, 8, 4, 0, 3, 256
 #define DFTU_PROJECT_SHAPES_PAIR(X) \
-    X(1, P_PAIR, 4, 8, 4, 1, 2, 256) X(2, P_PAIR, 4, 8, 4, 0, 2, 256) X(3, P_PAIR2, 4, 8, 8, 1, 2, 256) \
-    X(4, P_PAIR, 4, 8, 16, 1, 2, 256) X(5, P_PAIR, 8, 8, 4, 1, 2, 256) X(6, P_PAIR, 8, 8, 8, 1, 2, 256) \
-    X(7, P_PAIR, 8, 16, 4, 1, 2, 256)
-#define DFTU_PROJECT_DEFAULT_PAIR P_PAIR, 4, 8, 8, 1, 2, 256
+    X(1, P_PAIR, 8, 8, 8, 1, 2, 256) X(2, P_PAIR, 8, 8, 4, 5, 2, 256) X(3, P_PAIR, 8, 8, 16, 5, 2, 256) \
+    X(4, P_PAIR, 16, 8, 16, 5, 2, 256) X(5, P_PAIR, 8, 8, 16, 5, 4, 128) X(6, P_PAIR, 4, 8, 8, 5, 2, 256) \
+    X(7, P_PAIR, 8, 6, 8, 5, 2, 256)
+#define DFTU_PROJECT_DEFAULT_PAIR P_PAIR, 8, 8, 8, 5, 2, 256
 
 cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_f64_mode mode, int nbands,
                            int64_t sk, int64_t ss, int64_t sn, int variant, cudaStream_t st, bool gauge) {
@@ -930,7 +818,7 @@ cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_
     if (gauge) {   // one shape per arithmetic policy with the gauge phases (Sec. V)
         if (prec == DFTU_C64) e = run_project<P_F32, 8, 16, 8, 0, 2, 1>(v, a, st);
         else if (mode == DFTU_F64_NATIVE) e = run_project<P_F64, 8, 1, 4, 0, 2, 1>(v, a, st);
-        else e = run_project<P_PAIR, 4, 8, 4, 1, 2, 1>(v, a, st);
+        else e = run_project<P_PAIR, 8, 8, 8, 5, 2, 1>(v, a, st);
     } else if (prec == DFTU_C64) {
         switch (variant) {
             DFTU_PROJECT_SHAPES_F32(DFTU_CASE_F32)
@@ -960,7 +848,7 @@ cudaError_t launch_project_dirs(const View& v, const void* psi, dftu_prec prec, 
     // the fixed shapes of the gauge path, with and without the phases
     if (prec == DFTU_C64) e = gauge ? run_project<P_F32, 8, 16, 8, 0, 2, 1, 3>(v, a, st) : run_project<P_F32, 8, 16, 8, 0, 2, 0, 3>(v, a, st);
     else if (mode == DFTU_F64_NATIVE) e = gauge ? run_project<P_F64, 8, 1, 4, 0, 2, 1, 3>(v, a, st) : run_project<P_F64, 8, 1, 4, 0, 2, 0, 3>(v, a, st);
-    else e = gauge ? run_project<P_PAIR, 4, 8, 4, 1, 2, 1, 3>(v, a, st) : run_project<P_PAIR, 4, 8, 4, 1, 2, 0, 3>(v, a, st);
+    else e = gauge ? run_project<P_PAIR, 8, 8, 8, 5, 2, 1, 3>(v, a, st) : run_project<P_PAIR, 8, 8, 8, 5, 2, 0, 3>(v, a, st);
     if (e != cudaSuccess) return e;
     int64_t n = (int64_t)v.nk * v.ns * nbands * v.MT;
     for (int d = 0; d < 3; ++d) {
