@@ -236,7 +236,8 @@ dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, 
     std::vector<int> seg_atom;
     std::vector<std::vector<int>> seg_points;   // wrapped indices per segment (for colouring)
     c->tiles.clear();
-    int MT = 0, TM = 0, mat = 0;
+    std::vector<Tile> ptiles;   // the projection's tiling of the same segments (up to PTILE points)
+    int MT = 0, TM = 0, pTM = 0, mat = 0;
     int64_t phi_off = 0;
     const int64_t n0 = G.n[0], n1 = G.n[1], n2 = G.n[2];
     for (int a = 0; a < natoms; ++a) {
@@ -306,6 +307,20 @@ dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, 
                 c->tiles.push_back(t);
                 at += np;
             }
+            const int64_t npt = (len + PTILE - 1) / PTILE;
+            const int64_t pbase = len / npt, prem = len % npt;
+            at = first;
+            for (int64_t q = 0; q < npt; ++q) {
+                int np = (int)(pbase + (q < prem ? 1 : 0));
+                Tile t{};
+                t.atom = a; t.M = M; t.seg = segid; t.np = np; t.p0 = at;
+                t.phi0 = phi_off + (at - c->atom_p0[a]) * M;
+                t.moff = pTM;
+                t.color = 0;
+                pTM += M;
+                ptiles.push_back(t);
+                at += np;
+            }
         }
         for (int d = 0; d < 3; ++d) c->atom_umin[a][d] = umin[d];
         phi_off += nin * M;
@@ -361,11 +376,16 @@ dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, 
         }
     }
     // ---- per-atom tile ranges, species data, radial tables ----
-    std::vector<int> tbeg(natoms, 0), tend(natoms, 0);
+    std::vector<int> tbeg(natoms, 0), tend(natoms, 0), ptbeg(natoms, 0), ptend(natoms, 0);
     for (size_t t = 0; t < c->tiles.size(); ++t) {
         int a = c->tiles[t].atom;
         if (t == 0 || c->tiles[t - 1].atom != a) tbeg[a] = (int)t;
         tend[a] = (int)t + 1;
+    }
+    for (size_t t = 0; t < ptiles.size(); ++t) {
+        int a = ptiles[t].atom;
+        if (t == 0 || ptiles[t - 1].atom != a) ptbeg[a] = (int)t;
+        ptend[a] = (int)t + 1;
     }
     std::vector<int> aM(c->M), asp(natoms), amoff(c->moff), amat(c->mat_off);
     for (int a = 0; a < natoms; ++a) asp[a] = atoms[a].species;
@@ -388,7 +408,12 @@ dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, 
     double *d_pos, *d_rad, *d_rtab, *d_rdr, *d_fu, *d_fj, *d_coul;
     int *d_roff, *d_rnr;
     double2* d_segph;
+    Tile* dpt = nullptr;
+    int *d_ptb = nullptr, *d_pte = nullptr;
     e = upload(c, &dt, c->tiles);
+    if (e == cudaSuccess) e = upload(c, &dpt, ptiles);
+    if (e == cudaSuccess) e = upload(c, &d_ptb, ptbeg);
+    if (e == cudaSuccess) e = upload(c, &d_pte, ptend);
     if (e == cudaSuccess) e = upload(c, &d_idx, pt_idx);
     if (e == cudaSuccess) e = upload(c, &d_u, pt_u);
     unsigned char* d_first = nullptr;
@@ -419,6 +444,7 @@ dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, 
     v.maxM = *std::max_element(c->M.begin(), c->M.end());
     v.atom_pos = d_pos; v.atom_rad = d_rad; v.atom_M = d_aM; v.atom_species = d_asp; v.atom_moff = d_amoff;
     v.atom_mat_off = d_amat; v.atom_tile_beg = d_tb; v.atom_tile_end = d_te; v.species_coul_off = d_coff; v.species_M = d_spM;
+    v.ptiles = dpt; v.nptiles = (int)ptiles.size(); v.pTM = pTM; v.patom_tile_beg = d_ptb; v.patom_tile_end = d_pte;
     v.tiles = dt; v.pt_idx = d_idx; v.pt_u = d_u; v.pt_first = d_first; v.seg_T = d_segT; v.seg_phase = d_segph;
     c->h_coul_set.assign(nspecies, 0);
     c->h_fixU.assign(natoms, std::nan(""));

@@ -22,6 +22,7 @@ struct NvtxRange {
 };
 
 constexpr int TILE = 512;      // sphere points per tile (one CTA stages a tile in shared memory)
+constexpr int PTILE = 1024;    // sphere points per tile of the projection's own tiling (View::ptiles)
 constexpr int TILE_PAD = TILE + 128;   // staged orbital rows incl. zero padding read by chained loops (Q*CH <= 128)
 constexpr int MAXM = 7;        // orbitals per shell, l <= 3
 constexpr int IMG_RANGE = 2;   // lattice images |T| <= 2 cells per axis
@@ -77,6 +78,14 @@ struct View {
     const int* species_M;
 
     const Tile* tiles;
+    // The projection's own tiling: the same image segments cut into tiles of up to PTILE points (half
+    // the tile epilogues and partial sums of TILE-point tiles).  A projection launch that uses it swaps
+    // these into its copy of the View for tiles, ntiles, TM and atom_tile_beg/end, so k_tile_reduce
+    // follows unchanged; the partial buffer, sized for TM >= pTM, serves both.
+    const Tile* ptiles;
+    int nptiles, pTM;
+    const int* patom_tile_beg;
+    const int* patom_tile_end;
     const int* pt_idx;     // [S] wrapped linear index, GPU order
     const int* pt_u;       // [S][3] unfolded integer coordinates, GPU order
     const unsigned char* pt_first;   // [S] 1 if no tile of an earlier apply colour covers this grid point

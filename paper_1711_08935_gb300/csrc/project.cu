@@ -557,10 +557,18 @@ enum Pol { P_F64 = 0, P_PAIR = 1, P_F32 = 2, P_F32B2 = 4, P_F32B2F = 5 };
 // bands a lane carries at once
 template <int POL> struct LaneBands { static constexpr int value = (POL == P_F32B2 || POL == P_F32B2F) ? 2 : 1; };
 
+// Bytes of one staged orbital row (one point) for the largest shell maxM: FP64 values, (hi, hi, lo, lo)
+// per orbital for the FP32-pair policy, [hi pairs | lo pairs] for the complex64 policies.
+__host__ __device__ constexpr size_t phi_row_bytes(int pol, int maxM) {
+    return pol == P_F64 ? 8 * (size_t)maxM : pol == P_PAIR ? 16 * (size_t)maxM : 8 * (size_t)((maxM + 1) & ~1);
+}
+
 // One work item: tile `tile_id` of the system described by (v, a), spin/component index ks, every band of
 // band chunk `chunk` (NBG groups of BPC bands), against orbital table `dir` (0 unless the launch projects
-// onto several tables).  The tile is staged in shared memory once.
-template <int POL, int Q, int CH, int NBG, int PF, int G, int NT = CTA>
+// onto several tables).  The tile is staged in shared memory once.  TP: the tiling's largest tile (TILE,
+// or PTILE when the launch's View carries the projection's own tiling); shared memory holds TP grid
+// indices, then TP + 128 orbital rows (zeros past the tile), then the gauge phases.
+template <int POL, int Q, int CH, int NBG, int PF, int G, int NT = CTA, int TP = TILE>
 __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, int tile_id, int ks, int chunk,
                                              unsigned char* smem, int* s_pe, int dir = 0) {
     int* s_idx = reinterpret_cast<int*>(smem);
@@ -574,17 +582,18 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
 
     // ---- stage the tile once (grid indices, orbital rows, orbital exponent bound)
     if (threadIdx.x == 0) *s_pe = -200;
-    for (int i = threadIdx.x; i < TILE; i += NT) s_idx[i] = (i < t.np) ? v.pt_idx[t.p0 + i] : 0;
+    constexpr int TPAD = TP + (TILE_PAD - TILE);
+    for (int i = threadIdx.x; i < TP; i += NT) s_idx[i] = (i < t.np) ? v.pt_idx[t.p0 + i] : 0;
     __syncthreads();
     if (POL == P_F64) {
-        double* s_phi = reinterpret_cast<double*>(smem + TILE * sizeof(int));
-        for (int e = threadIdx.x; e < TILE * t.M; e += NT)
+        double* s_phi = reinterpret_cast<double*>(smem + TP * sizeof(int));
+        for (int e = threadIdx.x; e < TP * t.M; e += NT)
             s_phi[e] = (e < t.np * t.M) ? v.phi64[ph0 + e] : 0.0;
     } else if (POL == P_F32 || POL == P_F32B2 || POL == P_F32B2F) {
-        float* s_phf = reinterpret_cast<float*>(smem + TILE * sizeof(int));
+        float* s_phf = reinterpret_cast<float*>(smem + TP * sizeof(int));
         const int MP = (t.M + 1) & ~1;
         int pe = -200;
-        for (int e = threadIdx.x; e < TILE_PAD * MP; e += NT) {
+        for (int e = threadIdx.x; e < TPAD * MP; e += NT) {
             const int i = e / MP, m = e - i * MP;
             float hi = 0.f, lo = 0.f;
             if (i < t.np && m < t.M) { hi = v.phi_hi[ph0 + (int64_t)i * t.M + m]; lo = v.phi_lo[ph0 + (int64_t)i * t.M + m]; }
@@ -593,9 +602,9 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
             if (hi != 0.f) pe = max(pe, ((__float_as_int(hi) >> 23) & 0xFF) - 127 + 1);   // |hi| < 2^pe
         }
     } else {
-        float4* s_phi = reinterpret_cast<float4*>(smem + TILE * sizeof(int));
+        float4* s_phi = reinterpret_cast<float4*>(smem + TP * sizeof(int));
         int pe = -200;
-        for (int e = threadIdx.x; e < TILE_PAD * t.M; e += NT) {
+        for (int e = threadIdx.x; e < TPAD * t.M; e += NT) {
             float hi = 0.f, lo = 0.f;
             if (e < t.np * t.M) { hi = v.phi_hi[ph0 + e]; lo = v.phi_lo[ph0 + e]; }
             s_phi[e] = make_float4(hi, hi, lo, lo);
@@ -604,13 +613,13 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
         if (POL == P_PAIR) atomicMax(s_pe, pe);
     }
     // gauge phases of the tile's points (zeros past the tile), after the orbital rows of the largest shell
-    unsigned char* s_gauge = smem + TILE * sizeof(int) + (size_t)TILE_PAD * v.maxM * (POL == P_F64 ? sizeof(double) : sizeof(float4));
+    unsigned char* s_gauge = smem + TP * sizeof(int) + (size_t)TPAD * phi_row_bytes(POL, v.maxM);
     if (G) {
         if (POL == P_F64)
-            for (int i = threadIdx.x; i < TILE_PAD; i += NT)
+            for (int i = threadIdx.x; i < TPAD; i += NT)
                 reinterpret_cast<double2*>(s_gauge)[i] = (i < t.np) ? v.gauge_d[t.p0 + i] : make_double2(0.0, 0.0);
         else
-            for (int i = threadIdx.x; i < TILE_PAD; i += NT)
+            for (int i = threadIdx.x; i < TPAD; i += NT)
                 reinterpret_cast<float4*>(s_gauge)[i] = (i < t.np) ? v.gauge_f[t.p0 + i] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
@@ -624,7 +633,7 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
         const int64_t off = (int64_t)k * a.sk + (int64_t)s * a.ss + (int64_t)band * a.sn;
         if (POL == P_F32B2 || POL == P_F32B2F) {
             constexpr int FOLD = (POL == P_F32B2F) ? 1 : 0;
-            const float* s_phf = reinterpret_cast<const float*>(smem + TILE * sizeof(int));
+            const float* s_phf = reinterpret_cast<const float*>(smem + TP * sizeof(int));
             const float2* row0 = active ? reinterpret_cast<const float2*>(a.psi) + off : nullptr;
             const float2* row1 = (band + 1 < a.nbands) ? row0 + a.sn : nullptr;
             switch (t.M) {
@@ -634,7 +643,7 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
                 default: proj_body_f32x2<7, Q, CH, PF, FOLD>(v, t, ks, band, a.nbands, row0, row1, s_idx, s_phf, poff); break;
             }
         } else if (POL == P_F64) {
-            const double* s_phi = reinterpret_cast<const double*>(smem + TILE * sizeof(int));
+            const double* s_phi = reinterpret_cast<const double*>(smem + TP * sizeof(int));
             const double2* row = active ? reinterpret_cast<const double2*>(a.psi) + off : nullptr;
             const double2* s_g = reinterpret_cast<const double2*>(s_gauge);
             switch (t.M) {
@@ -644,7 +653,7 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
                 default: proj_body_f64<7, Q, G>(v, t, ks, band, row, s_idx, s_phi, s_g, poff); break;
             }
         } else if (POL == P_PAIR) {
-            const float4* s_phi = reinterpret_cast<const float4*>(smem + TILE * sizeof(int));
+            const float4* s_phi = reinterpret_cast<const float4*>(smem + TP * sizeof(int));
             const double2* row = active ? reinterpret_cast<const double2*>(a.psi) + off : nullptr;
             const double2* row_next = (active && g + 1 < NBG && band + BPC < a.nbands) ? row + (int64_t)BPC * a.sn : nullptr;
             const int pe = *s_pe;
@@ -656,7 +665,7 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
                 default: proj_body_pair<7, Q, CH, PF, G>(v, t, ks, band, row, row_next, s_idx, s_phi, pe, s_g, poff); break;
             }
         } else {
-            const float* s_phf = reinterpret_cast<const float*>(smem + TILE * sizeof(int));
+            const float* s_phf = reinterpret_cast<const float*>(smem + TP * sizeof(int));
             const float2* row = active ? reinterpret_cast<const float2*>(a.psi) + off : nullptr;
             const float4* s_g = reinterpret_cast<const float4*>(s_gauge);
             switch (t.M) {
@@ -671,13 +680,13 @@ __device__ __forceinline__ void project_item(const View& v, const ProjArgs& a, i
 
 // NDIR > 1: blockIdx.x = tile * NDIR + direction, so the CTAs of one tile and band chunk for the
 // NDIR orbital tables are neighbours in the launch and read the same states while they sit in L2.
-template <int POL, int Q, int CH, int NBG, int PF, int MINB, int G, int NDIR = 1, int NT = CTA>
+template <int POL, int Q, int CH, int NBG, int PF, int MINB, int G, int NDIR = 1, int NT = CTA, int TP = TILE>
 __global__ void __launch_bounds__(NT, MINB) k_project(View v, ProjArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_pe;
     const int tile = (NDIR == 1) ? (int)blockIdx.x : (int)blockIdx.x / NDIR;
     const int dir = (NDIR == 1) ? 0 : (int)blockIdx.x % NDIR;
-    project_item<POL, Q, CH, NBG, PF, G, NT>(v, a, tile, blockIdx.z, blockIdx.y, smem, &s_pe, dir);
+    project_item<POL, Q, CH, NBG, PF, G, NT, TP>(v, a, tile, blockIdx.z, blockIdx.y, smem, &s_pe, dir);
 }
 
 // Persistent form over many systems: every CTA takes (system, tile, k*spin) items from a counter until
@@ -771,50 +780,84 @@ __global__ void k_tile_reduce_batch(const View* __restrict__ views, const ProjAr
     tile_reduce_elem(views[blockIdx.y], args[blockIdx.y].nbands, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-template <int POL, int Q, int CH, int NBG, int PF, int MINB = 2, int G = 0, int NDIR = 1, int NT = CTA>
-static cudaError_t run_project(const View& v, const ProjArgs& a, cudaStream_t st) {
+// Whether MINB CTAs of fn with smem bytes of dynamic shared memory fit on one SM (cached per kernel and size).
+static bool fits_per_sm(const void* fn, int nt, size_t smem, int minb) {
+    static std::mutex mu;
+    static std::vector<std::pair<std::pair<const void*, size_t>, bool>> seen;
+    std::lock_guard<std::mutex> lock(mu);
+    for (auto& s : seen)
+        if (s.first.first == fn && s.first.second == smem) return s.second;
+    int n = 0;
+    // the attribute only ever grows (smem_configured keeps the largest size set), so a smaller system
+    // asked about later cannot leave it below what an earlier launch configured
+    cudaError_t e = cudaSuccess;
+    if (!smem_configured(fn, (int)smem)) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, nt, smem) != cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
+    }
+    seen.push_back({{fn, smem}, n >= minb});
+    return n >= minb;
+}
+
+// One projection launch.  TP = PTILE runs over the projection's own tiling (View::ptiles) when MINB CTAs
+// with that shared memory still fit on an SM, and over the TILE tiling otherwise; *used receives the View
+// the launch ran with, whose tiling the tile reduce must follow.
+template <int POL, int Q, int CH, int NBG, int PF, int MINB = 2, int G = 0, int NDIR = 1, int NT = CTA, int TP = TILE>
+static cudaError_t run_project(const View& v, const ProjArgs& a, cudaStream_t st, View* used = nullptr) {
     static_assert(Q * CH <= TILE_PAD - TILE, "chained loops read up to Q*CH rows past the tile");
-    size_t smem = TILE * sizeof(int) + (size_t)TILE_PAD * v.maxM * (POL == P_F64 ? sizeof(double) : sizeof(float4)) +
-                  (G ? (size_t)TILE_PAD * 16 : 0);
-    auto fn = k_project<POL, Q, CH, NBG, PF, MINB, G, NDIR, NT>;
+    static_assert(TP == TILE || TP == PTILE, "a tiling the View carries");
+    constexpr int TPAD = TP + (TILE_PAD - TILE);
+    size_t smem = TP * sizeof(int) + (size_t)TPAD * phi_row_bytes(POL, v.maxM) + (G ? (size_t)TPAD * 16 : 0);
+    auto fn = k_project<POL, Q, CH, NBG, PF, MINB, G, NDIR, NT, TP>;
+    View vl = v;
+    if (TP != TILE) {
+        if (!fits_per_sm((const void*)fn, NT, smem, MINB)) return run_project<POL, Q, CH, NBG, PF, MINB, G, NDIR, NT, TILE>(v, a, st, used);
+        vl.tiles = v.ptiles; vl.ntiles = v.nptiles; vl.TM = v.pTM;
+        vl.atom_tile_beg = v.patom_tile_beg; vl.atom_tile_end = v.patom_tile_end;
+    }
+    if (used) *used = vl;
     cudaError_t e = cudaSuccess;
     if (!smem_configured((const void*)fn, (int)smem)) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     constexpr int BPC = (NT / 32) * (32 / Q) * LaneBands<POL>::value;
-    dim3 grid(v.ntiles * NDIR, (a.nbands + BPC * NBG - 1) / (BPC * NBG), v.nk * v.ns);
-    fn<<<grid, NT, smem, st>>>(v, a);
+    dim3 grid(vl.ntiles * NDIR, (a.nbands + BPC * NBG - 1) / (BPC * NBG), vl.nk * vl.ns);
+    fn<<<grid, NT, smem, st>>>(vl, a);
     return cudaGetLastError();
 }
 
-// The default shape of a table row (variant 0): run_project with its thread count in the last place.
-template <int POL, int Q, int CH, int NBG, int PF, int MINB, int NT>
-static cudaError_t run_project_default(const View& v, const ProjArgs& a, cudaStream_t st) {
-    return run_project<POL, Q, CH, NBG, PF, MINB, 0, 1, NT>(v, a, st);
+// The default shape of a table row (variant 0): run_project with its thread count and tiling in the last
+// places.
+template <int POL, int Q, int CH, int NBG, int PF, int MINB, int NT, int TP>
+static cudaError_t run_project_default(const View& v, const ProjArgs& a, cudaStream_t st, View* used) {
+    return run_project<POL, Q, CH, NBG, PF, MINB, 0, 1, NT, TP>(v, a, st, used);
 }
 
 // The shapes selectable with dftu_set_kernel_variant, listed once for the single-system and the batched
 // launches: X(variant, policy, lanes per band Q, points per chain, band groups per CTA, L2 prefetch,
-// minimum blocks per SM, threads per CTA).  Variant 0 is the default case of each switch.  P_F32B2 is
-// the complex64 form with two bands per lane, P_F32B2F the same with each product's hi and lo halves
-// folded into one sum, P_F32 one band per lane.  PAIR L2 prefetch: 1 = the next chain, 5 = also the
-// next band's first chain.
+// minimum blocks per SM, threads per CTA, tile size).  Variant 0 is the default case of each switch.
+// P_F32B2 is the complex64 form with two bands per lane, P_F32B2F the same with each product's hi and lo
+// halves folded into one sum, P_F32 one band per lane.  PAIR L2 prefetch: 1 = the next chain, 5 = also
+// the next band's first chain.  Tile size PTILE selects the projection's own tiling (single-system
+// launches; batched launches use TILE, on which PAIR variant 1 is the default shape).
 #define DFTU_PROJECT_SHAPES_F32(X) \
-    X(1, P_F32B2F, 16, 8, 4, 1, 3, 256) X(2, P_F32B2F, 8, 8, 4, 0, 3, 256) X(3, P_F32B2, 8, 8, 4, 0, 2, 256) \
-    X(4, P_F32B2F, 16, 8, 4, 0, 2, 256) X(5, P_F32B2F, 16, 8, 8, 0, 3, 256) X(6, P_F32B2F, 16, 6, 4, 0, 3, 256) \
-    X(7, P_F32, 8, 16, 8, 0, 2, 256)
-#define DFTU_PROJECT_DEFAULT_F32 P_F32B2F, 16, 8, 4, 0, 3, 256
+    X(1, P_F32B2F, 16, 8, 4, 0, 3, 256, PTILE) X(2, P_F32B2F, 8, 8, 4, 0, 3, 256, TILE) X(3, P_F32B2, 8, 8, 4, 0, 2, 256, TILE) \
+    X(4, P_F32B2F, 16, 8, 4, 0, 2, 256, TILE) X(5, P_F32B2F, 16, 8, 8, 0, 3, 256, TILE) \
+    X(6, P_F32B2F, 16, 6, 4, 0, 3, 256, TILE) X(7, P_F32, 8, 16, 8, 0, 2, 256, TILE)
+#define DFTU_PROJECT_DEFAULT_F32 P_F32B2F, 16, 8, 4, 0, 3, 256, TILE
 #define DFTU_PROJECT_SHAPES_PAIR(X) \
-    X(1, P_PAIR, 8, 8, 8, 1, 2, 256) X(2, P_PAIR, 8, 8, 4, 5, 2, 256) X(3, P_PAIR, 8, 8, 16, 5, 2, 256) \
-    X(4, P_PAIR, 16, 8, 16, 5, 2, 256) X(5, P_PAIR, 8, 8, 16, 5, 4, 128) X(6, P_PAIR, 4, 8, 8, 5, 2, 256) \
-    X(7, P_PAIR, 8, 6, 8, 5, 2, 256)
-#define DFTU_PROJECT_DEFAULT_PAIR P_PAIR, 8, 8, 8, 5, 2, 256
+    X(1, P_PAIR, 8, 8, 8, 5, 2, 256, TILE) X(2, P_PAIR, 8, 8, 4, 5, 2, 256, PTILE) X(3, P_PAIR, 8, 8, 16, 5, 2, 256, PTILE) \
+    X(4, P_PAIR, 16, 8, 16, 5, 2, 256, PTILE) X(5, P_PAIR, 8, 8, 8, 1, 2, 256, PTILE) X(6, P_PAIR, 8, 8, 4, 5, 2, 256, TILE) \
+    X(7, P_PAIR, 8, 6, 8, 5, 2, 256, PTILE)
+#define DFTU_PROJECT_DEFAULT_PAIR P_PAIR, 8, 8, 8, 5, 2, 256, PTILE
 
 cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_f64_mode mode, int nbands,
                            int64_t sk, int64_t ss, int64_t sn, int variant, cudaStream_t st, bool gauge) {
     ProjArgs a{psi, sk, ss, sn, nbands};
     cudaError_t e;
-#define DFTU_CASE_F32(i, POL, Q, CH, NBG, PF, MB, NT) case i: e = run_project<POL, Q, CH, NBG, PF, MB, 0, 1, NT>(v, a, st); break;
-#define DFTU_CASE_PAIR(i, POL, Q, CH, NBG, PF, MB, NT) case i: e = run_project<POL, Q, CH, NBG, PF, MB, 0, 1, NT>(v, a, st); break;
+    View vp = v;   // the View the projection ran with: its tiling feeds the tile reduce
+#define DFTU_CASE_F32(i, POL, Q, CH, NBG, PF, MB, NT, TP) case i: e = run_project<POL, Q, CH, NBG, PF, MB, 0, 1, NT, TP>(v, a, st, &vp); break;
+#define DFTU_CASE_PAIR(i, POL, Q, CH, NBG, PF, MB, NT, TP) case i: e = run_project<POL, Q, CH, NBG, PF, MB, 0, 1, NT, TP>(v, a, st, &vp); break;
     if (gauge) {   // one shape per arithmetic policy with the gauge phases (Sec. V)
         if (prec == DFTU_C64) e = run_project<P_F32, 8, 16, 8, 0, 2, 1>(v, a, st);
         else if (mode == DFTU_F64_NATIVE) e = run_project<P_F64, 8, 1, 4, 0, 2, 1>(v, a, st);
@@ -822,21 +865,21 @@ cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_
     } else if (prec == DFTU_C64) {
         switch (variant) {
             DFTU_PROJECT_SHAPES_F32(DFTU_CASE_F32)
-            default: e = run_project_default<DFTU_PROJECT_DEFAULT_F32>(v, a, st); break;
+            default: e = run_project_default<DFTU_PROJECT_DEFAULT_F32>(v, a, st, &vp); break;
         }
     } else if (mode == DFTU_F64_NATIVE) {
         e = run_project<P_F64, 8, 1, 4, 0>(v, a, st);
     } else {
         switch (variant) {
             DFTU_PROJECT_SHAPES_PAIR(DFTU_CASE_PAIR)
-            default: e = run_project_default<DFTU_PROJECT_DEFAULT_PAIR>(v, a, st); break;
+            default: e = run_project_default<DFTU_PROJECT_DEFAULT_PAIR>(v, a, st, &vp); break;
         }
     }
 #undef DFTU_CASE_F32
 #undef DFTU_CASE_PAIR
     if (e != cudaSuccess) return e;
     int64_t n = (int64_t)v.nk * v.ns * nbands * v.MT;
-    k_tile_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(v, nbands);
+    k_tile_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(vp, nbands);
     return cudaGetLastError();
 }
 
@@ -864,7 +907,7 @@ cudaError_t launch_project_dirs(const View& v, const void* psi, dftu_prec prec, 
 
 template <int POL, int Q, int CH, int NBG, int PF, int MINB = 2, int NT = CTA>
 static cudaError_t run_project_batch(const BatchLaunch& b, cudaStream_t st) {
-    size_t smem = TILE * sizeof(int) + (size_t)TILE_PAD * b.maxM * (POL == P_F64 ? sizeof(double) : sizeof(float4));
+    size_t smem = TILE * sizeof(int) + (size_t)TILE_PAD * phi_row_bytes(POL, b.maxM);
     cudaError_t e = cudaSuccess;
     auto fn = k_project_batch<POL, Q, CH, NBG, PF, MINB, NT>;
     if (!smem_configured((const void*)fn, (int)smem)) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -881,21 +924,27 @@ static cudaError_t run_project_batch(const BatchLaunch& b, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// The default shape of a table row for the batched launch (always the TILE tiling).
+template <int POL, int Q, int CH, int NBG, int PF, int MINB, int NT, int TP>
+static cudaError_t run_project_batch_default(const BatchLaunch& b, cudaStream_t st) {
+    return run_project_batch<POL, Q, CH, NBG, PF, MINB, NT>(b, st);
+}
+
 cudaError_t launch_project_batch(const BatchLaunch& b, dftu_prec prec, dftu_f64_mode mode, int variant, cudaStream_t st) {
     cudaError_t e;
-#define DFTU_CASE_F32(i, POL, Q, CH, NBG, PF, MB, NT) case i: e = run_project_batch<POL, Q, CH, NBG, PF, MB, NT>(b, st); break;
-#define DFTU_CASE_PAIR(i, POL, Q, CH, NBG, PF, MB, NT) case i: e = run_project_batch<POL, Q, CH, NBG, PF, MB, NT>(b, st); break;
+#define DFTU_CASE_F32(i, POL, Q, CH, NBG, PF, MB, NT, TP) case i: e = run_project_batch<POL, Q, CH, NBG, PF, MB, NT>(b, st); break;
+#define DFTU_CASE_PAIR(i, POL, Q, CH, NBG, PF, MB, NT, TP) case i: e = run_project_batch<POL, Q, CH, NBG, PF, MB, NT>(b, st); break;
     if (prec == DFTU_C64) {
         switch (variant) {
             DFTU_PROJECT_SHAPES_F32(DFTU_CASE_F32)
-            default: e = run_project_batch<DFTU_PROJECT_DEFAULT_F32>(b, st); break;
+            default: e = run_project_batch_default<DFTU_PROJECT_DEFAULT_F32>(b, st); break;
         }
     } else if (mode == DFTU_F64_NATIVE) {
         e = run_project_batch<P_F64, 8, 1, 4, 0>(b, st);
     } else {
         switch (variant) {
             DFTU_PROJECT_SHAPES_PAIR(DFTU_CASE_PAIR)
-            default: e = run_project_batch<DFTU_PROJECT_DEFAULT_PAIR>(b, st); break;
+            default: e = run_project_batch_default<DFTU_PROJECT_DEFAULT_PAIR>(b, st); break;
         }
     }
 #undef DFTU_CASE_F32

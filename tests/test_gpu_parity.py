@@ -353,3 +353,28 @@ def test_access_ceiling_pass_leaves_states_unchanged(dtype):
     h = dftu.handle_for_system(C.periodic_two_atoms(), 4)
     assert h.lib.dftu_access_ceiling(h.h, None, 0, 4, 8000, 0, None) == dftu.DFTU_ERR_INVALID_ARG
     h.close()
+
+
+def _periodic_p_shell():
+    g = synth.Grid((18, 18, 18), (0.45, 0.45, 0.45), (0.0, 0.0, 0.0), periodic=True)
+    return synth.System(g, [synth.Atom((4.0, 4.1, 3.9), 0, 1, 3.2)], [synth.hydrogenic_radial(2, 1, 2.5)],
+                        np.zeros((1, 3)), np.ones(1), nspin=2, name="periodic p shell")
+
+
+def test_projection_tilings_across_shell_sizes():
+    """The complex128 projection's default runs on 1024-point tiles, whose staged orbital rows need more
+    shared memory for larger shells. Systems with different largest shells projected in turn in one
+    process (d, p only, p + f, d again) must each launch with their own size; the p + f system, whose
+    CTAs no longer fit two per SM, falls back to the 512-point tiling. Each against the oracle."""
+    nb = 40
+    for make in (synth.small_oxide_system, _periodic_p_shell, isolated_aniso, synth.small_oxide_system):
+        s = make()
+        psi = C.states_np(s, nb, seed=21)
+        ref = O.project(s, O.setup_atoms(s), psi)
+        h = dftu.handle_for_system(s, nb)
+        h.project(torch.from_numpy(psi).cuda())
+        p = split_p(s, h.projections(nb))
+        for I in range(len(s.atoms)):
+            assert rel(p[I], ref[I]) < 1e-12, (s.name, I)
+        assert h.sync_status() == dftu.DFTU_OK
+        h.close()
