@@ -35,7 +35,7 @@ WORKLOAD = "oxide supercell 96^3 h=0.25, 8 TM(3d,R4.5)+8 O(2p,R3.5), 256 bands, 
 # DRAM bytes per state (one band of one k-point and spin) measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum) on the 64-band oxide case for the kernel variants named here; see
 # profiles/project_apply_oxide_small.md.  Valid only while that variant is the one timed.
-NCU_TRAFFIC_PER_STATE = {("project", 0): (801.56e6 + 8.19e6) / 128,
+NCU_TRAFFIC_PER_STATE = {("project", 0): (802.03e6 + 5.63e6) / 128,
                          ("apply", 0): (800.74e6 + 566.71e6) / 128}
 # The same for the fixed complex128 shapes of the gauge-invariant path; see
 # profiles/gauge_project_apply_current_oxide_small.md.
