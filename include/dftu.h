@@ -142,8 +142,9 @@ dftu_status dftu_set_f64_mode(dftu_handle h, dftu_f64_mode mode);
 /* Kernel variant for one of the streaming kernels (the library's autotuner in the Python binding picks
  * them by timing): which = 0 projection of complex128 states, 1 projection of complex64 states,
  * 2 apply of complex128 states, 3 apply of complex64 states; variant indexes a fixed table of
- * (lanes per band, points per chain, band groups per CTA) shapes, 0 = default.  Results do not depend
- * on the variant beyond floating-point summation order. */
+ * (lanes per band, points per chain, band groups per CTA, prefetch, tile size) shapes, 0 = default.
+ * Results do not depend on the variant beyond floating-point summation order.  Batched calls
+ * (dftu_batch_*) run every projection shape on 512-point tiles. */
 dftu_status dftu_set_kernel_variant(dftu_handle h, int which, int variant);
 
 /* Number of kernel variants available for `which` (see dftu_set_kernel_variant); 0 for a bad `which`. */

@@ -463,11 +463,12 @@ static cudaError_t run_apply(const View& v, ApplyArgs a, const int* color_order,
 
 // The shapes selectable with dftu_set_kernel_variant, listed once for the single-system and the batched
 // launches: X(variant, lanes per band Q, band groups per CTA, points in flight per lane, L2 prefetch).
-// Variant 0, and 6 and 7, take the default case of each switch.
+// Variant 0 takes the default case of each switch.
 #define DFTU_APPLY_SHAPES_F32(X) X(1, A_F32, 8, 4, 8, 1) X(2, A_F32, 16, 4, 8, 1) X(3, A_F32P, 8, 4, 8, 1) \
-    X(4, A_F32P, 8, 4, 16, 1) X(5, A_F32P, 16, 4, 4, 1)
+    X(4, A_F32P, 8, 4, 16, 1) X(5, A_F32P, 16, 4, 4, 1) X(6, A_F32P, 16, 8, 4, 1) X(7, A_F32P, 8, 8, 8, 1)
 #define DFTU_APPLY_DEFAULT_F32 A_F32P, 16, 4, 8, 1
-#define DFTU_APPLY_SHAPES_PAIR(X) X(1, 8, 4, 4, 1) X(2, 16, 4, 2, 1) X(3, 8, 4, 8, 1) X(4, 16, 2, 4, 1) X(5, 16, 4, 4, 0)
+#define DFTU_APPLY_SHAPES_PAIR(X) X(1, 8, 4, 4, 1) X(2, 16, 4, 2, 1) X(3, 8, 4, 8, 1) X(4, 16, 2, 4, 1) X(5, 16, 4, 4, 0) \
+    X(6, 16, 8, 2, 1) X(7, 8, 8, 4, 1)
 #define DFTU_APPLY_DEFAULT_PAIR 16, 4, 4, 1
 
 cudaError_t launch_apply(const View& v, void* psi, dftu_prec prec, dftu_f64_mode mode, int nbands,
