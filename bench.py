@@ -636,35 +636,64 @@ def run_rt(args):
     tuned = autotune(h, psi, out=scratch)
     del scratch
     torch.cuda.empty_cache()
-    work = None
     n0 = (psi.abs() ** 2).sum(-1).double() * s.grid.dV
     dt = 0.01
-    side = torch.cuda.Stream()
-    side.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(side):
-        for _ in range(args.warmup):
-            h.taylor_step(psi, work, f, dt)
-    torch.cuda.current_stream().wait_stream(side)
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g):
-        for _ in range(args.rt_steps):
-            h.taylor_step(psi, work, f, dt)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(0)
-    clocks.start()
-    clocks.mark()
-    e0.record()
-    g.replay()
-    e1.record()
-    torch.cuda.synchronize()
-    clocks.mark()
-    clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.rt_steps
-    n1 = (psi.abs() ** 2).sum(-1).double() * s.grid.dV
     S = _sphere_bytes(h, len(s.atoms))
     unit = S * 8 * nb * s.nk                      # one read of every sphere point of every state (complex64)
-    step_bytes = 3 * unit                         # one projection + one read-modify-write apply per step
+
+    def graph_of(fn, warm):
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(args.warmup):
+                warm()
+        torch.cuda.current_stream().wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        torch.cuda.synchronize()
+        return g
+
+    def time_graph(g, sampler=None):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if sampler:
+            sampler.mark()
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.mark()
+        return e0.elapsed_time(e1)
+
+    # all steps in one dftu_taylor_steps call: each step's scatter also gathers the updated states for the
+    # next step, so a step reads and writes every sphere point once (plus the first step's gather)
+    g = graph_of(lambda: h.taylor_steps(psi, f, dt, args.rt_steps), lambda: h.taylor_steps(psi, f, dt, 1))
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms = time_graph(g, clocks) / args.rt_steps
+    clk = clocks.stop()
+    n1 = (psi.abs() ** 2).sum(-1).double() * s.grid.dV
+    del g
+    # the same steps one projection and one apply at a time (dftu_taylor_step), for comparison
+    n_single = max(10, args.rt_steps // 4)
+    g1 = graph_of(lambda: [h.taylor_step(psi, None, f, dt) for _ in range(n_single)], lambda: h.taylor_step(psi, None, f, dt))
+    ms1 = time_graph(g1) / n_single
+    del g1
+
+    def ceiling_ms(rmw, reps=5):
+        for _ in range(2):
+            h.access_ceiling(psi, rmw)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for e0, e1 in evs:
+            e0.record()
+            h.access_ceiling(psi, rmw)
+            e1.record()
+        torch.cuda.synchronize()
+        return statistics.median(e0.elapsed_time(e1) for e0, e1 in evs)
+
+    gather_ms, rmw_ms = ceiling_ms(False), ceiling_ms(True)
+    step_bytes = 2 * unit + unit / args.rt_steps   # read + write of every sphere point per step, first gather
     peak, src = measured_peaks()
     return ({
         "metric": METRIC, "value": round(step_bytes / (ms * 1e-3) / 1e9, 2), "unit": UNIT, "n_gpus": 1,
@@ -673,7 +702,16 @@ def run_rt(args):
         "config": {"workload": "real-time Taylor-4 steps: 64 atoms / 3 species (R 3.5/4.5/5.0), periodic 128^3 h=0.3, "
                                "512 c64 bands, 4 k, V_U and ACBN0 U/J rebuilt every step, all steps in one CUDA graph",
                    "sphere_points_sum": S, "steps_in_graph": args.rt_steps, "dt": dt},
+        "bytes_per_step": "2 state passes (the scatter of step s gathers for step s+1) + the first gather / steps",
         "steps_per_s": round(1e3 / ms, 2), "graph_ms_total": round(ms * args.rt_steps, 2),
+        "one_step_at_a_time": {"ms_per_step": round(ms1, 4), "steps": n_single,
+                               "GBps": round(3 * unit / (ms1 * 1e-3) / 1e9, 2),
+                               "note": "dftu_taylor_step per step: one projection and one apply (3 state passes)",
+                               "speedup_of_fused": round(ms1 / ms, 3)},
+        "access_ceiling": {"c64_gather_GBps": round(unit / (gather_ms * 1e-3) / 1e9, 1),
+                           "c64_rmw_GBps": round(2 * unit / (rmw_ms * 1e-3) / 1e9, 1),
+                           "step_floor_ms": round(rmw_ms, 4),
+                           "frac_of_ceiling": round(rmw_ms / ms, 4)},
         "norm_drift_max": float((n1 - n0).abs().max()), "state_generation_s": round(gen_s, 1),
         "peak": peak, "peak_source": src, "frac_of_peak": round(step_bytes / (ms * 1e-3) / 1e9 / peak, 4), "clocks": clk,
         "U_eV_first_atoms": [round(x * dftu.HARTREE_EV, 5) for x in h.results()["U"][:6]], "tuning": tuned})

@@ -194,6 +194,20 @@ dftu_status dftu_apply(dftu_handle h, void* psi_out, dftu_prec prec, int nbands,
 dftu_status dftu_taylor_step(dftu_handle h, void* psi, void* work, dftu_prec prec, int nbands, int64_t ld_band,
                              const double* f, double dt, int order, dftu_stream stream);
 
+/* nsteps successive real-time steps of dftu_taylor_step (Sec. V, Eq. 15) on psi, each with occupations,
+ * U, J and V_U rebuilt from that step's incoming states.  Between two steps nothing but the Hubbard term
+ * changes psi, so the gather of step s+1 reads the values the scatter of step s writes: for complex64
+ * collinear or unpolarised states without a vector potential, the scatter kernel projects the values it
+ * has just written on every tile that no later apply colour touches (the projection of the remaining
+ * tiles, where spheres overlap, runs after the last colour), and each step reads and writes every sphere
+ * point once.  Other states run the steps one projection and one apply at a time.  The projections use
+ * the complex64 projection's arithmetic (compensated FP32 products, FP32 sums within a tile, FP64 across
+ * tiles).  Afterwards the handle's projections are those of the outgoing psi, and its occupations, U, J
+ * and V those of the last step's incoming psi.  order <= 8, nsteps >= 1.  Launches only, no host
+ * synchronisation and no allocation: a CUDA graph can capture it. */
+dftu_status dftu_taylor_steps(dftu_handle h, void* psi, dftu_prec prec, int nbands, int64_t ld_band, const double* f,
+                              double dt, int order, int nsteps, dftu_stream stream);
+
 /* Gauge-invariant Hubbard operator under a uniform vector potential A (Sec. V, Eq. 16).  Every
  * localised orbital carries the phase exp(-i A.d), d = r - R_I measured from its own atom (the
  * atom-relative reading of Eq. 16), so after this call

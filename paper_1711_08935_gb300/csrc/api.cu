@@ -234,7 +234,6 @@ dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, 
     c->atom_umin.assign(natoms, std::vector<int>(3, 0));
     std::vector<int> pt_idx, pt_u, seg_T;
     std::vector<int> seg_atom;
-    std::vector<std::vector<int>> seg_points;   // wrapped indices per segment (for colouring)
     c->tiles.clear();
     std::vector<Tile> ptiles;   // the projection's tiling of the same segments (up to PTILE points)
     int MT = 0, TM = 0, pTM = 0, mat = 0;
@@ -279,7 +278,6 @@ dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, 
             int tx = img % 5 - IMG_RANGE, ty = (img / 5) % 5 - IMG_RANGE, tz = img / 25 - IMG_RANGE;
             if (!G.periodic) tx = ty = tz = 0;
             seg_T.push_back(tx); seg_T.push_back(ty); seg_T.push_back(tz);
-            seg_points.emplace_back();
             int64_t first = (int64_t)pt_idx.size();
             for (int64_t b : L) {
                 int ix = box_lo[3 * a] + (int)(b % bx);
@@ -290,7 +288,6 @@ dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, 
                 pt_idx.push_back(idx);
                 pt_u.push_back(ix); pt_u.push_back(jy); pt_u.push_back(kz);
                 umin[0] = std::min(umin[0], ix); umin[1] = std::min(umin[1], jy); umin[2] = std::min(umin[2], kz);
-                seg_points.back().push_back(idx);
                 c->canon_to_gpu[a][canon_rank[b]] = local++;
             }
             int64_t len = (int64_t)pt_idx.size() - first;
@@ -330,24 +327,27 @@ dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, 
     c->mat_total = mat;
     c->S = (int64_t)pt_idx.size();
     c->phi_total = phi_off;
-    // ---- apply colouring: greedy, segments sharing a grid point get different colours ----
+    // ---- apply colouring: greedy over tiles, tiles sharing a grid point get different colours ----
+    // Colouring tiles rather than whole segments keeps every tile away from an overlap in colour 0, so
+    // the later colours hold only the few tiles that reach a shared point.
     const int nseg = (int)seg_atom.size();
-    std::vector<int> seg_color(nseg, -1);
     {
         const int64_t npts = n0 * n1 * n2;
         std::vector<std::vector<unsigned char>> used;
-        for (int s = 0; s < nseg; ++s) {
+        std::vector<int> tile_color(c->tiles.size(), 0);
+        for (size_t t = 0; t < c->tiles.size(); ++t) {
+            const Tile& tt = c->tiles[t];
             int col = 0;
             for (;; ++col) {
                 if (col == (int)used.size()) used.emplace_back(npts, 0);
                 bool clash = false;
-                for (int idx : seg_points[s])
-                    if (used[col][idx]) { clash = true; break; }
+                for (int i = 0; i < tt.np; ++i)
+                    if (used[col][pt_idx[tt.p0 + i]]) { clash = true; break; }
                 if (!clash) break;
                 if (col >= 255) return fail(c, DFTU_ERR_INVALID_ARG, "setup_atoms: too many overlapping spheres");
             }
-            seg_color[s] = col;
-            for (int idx : seg_points[s]) used[col][idx] = 1;
+            tile_color[t] = col;
+            for (int i = 0; i < tt.np; ++i) used[col][pt_idx[tt.p0 + i]] = 1;
         }
         int ncol = used.size();
         c->color_beg.assign(ncol + 1, 0);
@@ -355,7 +355,7 @@ dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, 
         for (int col = 0; col < ncol; ++col) {
             c->color_beg[col] = (int)c->color_order.size();
             for (size_t t = 0; t < c->tiles.size(); ++t)
-                if (seg_color[c->tiles[t].seg] == col) {
+                if (tile_color[t] == col) {
                     c->tiles[t].color = col;
                     c->color_order.push_back((int)t);
                 }
@@ -373,6 +373,23 @@ dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, 
                 pt_first[t.p0 + i] = written[idx] ? 0 : 1;
                 written[idx] = 1;
             }
+        }
+    }
+    // ---- final tiles: no tile of a later apply colour covers any of their points, so the values an apply
+    // of their colour leaves are the values after the whole apply (the fused scatter-gather projects them)
+    std::vector<unsigned char> tile_final(c->tiles.size(), 1);
+    std::vector<Tile> nonfinal;
+    {
+        std::vector<int> last((size_t)(n0 * n1 * n2), -1);
+        for (int ti : c->color_order) {
+            const Tile& t = c->tiles[ti];
+            for (int i = 0; i < t.np; ++i) last[pt_idx[t.p0 + i]] = ti;
+        }
+        for (int ti : c->color_order) {
+            const Tile& t = c->tiles[ti];
+            for (int i = 0; i < t.np; ++i)
+                if (last[pt_idx[t.p0 + i]] != ti) { tile_final[ti] = 0; break; }
+            if (!tile_final[ti]) nonfinal.push_back(t);
         }
     }
     // ---- per-atom tile ranges, species data, radial tables ----
@@ -418,6 +435,10 @@ dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, 
     if (e == cudaSuccess) e = upload(c, &d_u, pt_u);
     unsigned char* d_first = nullptr;
     if (e == cudaSuccess) e = upload(c, &d_first, pt_first);
+    unsigned char* d_tfinal = nullptr;
+    if (e == cudaSuccess) e = upload(c, &d_tfinal, tile_final);
+    c->n_nonfinal = (int)nonfinal.size();
+    if (e == cudaSuccess && !nonfinal.empty()) e = upload(c, &c->d_nonfinal_tiles, nonfinal);
     if (e == cudaSuccess) e = upload(c, &d_segT, seg_T);
     if (e == cudaSuccess) e = dalloc(c, &d_segph, (size_t)nseg * c->nk);
     if (e == cudaSuccess) e = upload(c, &d_aM, aM);
@@ -445,7 +466,7 @@ dftu_status dftu_setup_atoms(dftu_handle h, int natoms, const dftu_atom* atoms, 
     v.atom_pos = d_pos; v.atom_rad = d_rad; v.atom_M = d_aM; v.atom_species = d_asp; v.atom_moff = d_amoff;
     v.atom_mat_off = d_amat; v.atom_tile_beg = d_tb; v.atom_tile_end = d_te; v.species_coul_off = d_coff; v.species_M = d_spM;
     v.ptiles = dpt; v.nptiles = (int)ptiles.size(); v.pTM = pTM; v.patom_tile_beg = d_ptb; v.patom_tile_end = d_pte;
-    v.tiles = dt; v.pt_idx = d_idx; v.pt_u = d_u; v.pt_first = d_first; v.seg_T = d_segT; v.seg_phase = d_segph;
+    v.tiles = dt; v.tile_final = d_tfinal; v.pt_idx = d_idx; v.pt_u = d_u; v.pt_first = d_first; v.seg_T = d_segT; v.seg_phase = d_segph;
     c->h_coul_set.assign(nspecies, 0);
     c->h_fixU.assign(natoms, std::nan(""));
     v.coul = d_coul; v.coul_set = d_cset; v.fixU = d_fu; v.fixJ = d_fj;
@@ -806,6 +827,56 @@ dftu_status dftu_taylor_step(dftu_handle h, void* psi, void* work, dftu_prec pre
     if (e == cudaSuccess)
         e = launch_apply(c->v, psi, prec, c->f64_mode, nbands, sk, ss, sn, c->d_coef_one, c->d_color_order, c->color_beg, va, 1, st, G);
     if (e != cudaSuccess) return cuda_fail(c, e, "taylor_step");
+    c->last_stream = st;
+    c->proj_ready = c->occ_ready = c->pot_ready = true;
+    c->proj_nbands = nbands;
+    return DFTU_OK;
+}
+
+dftu_status dftu_taylor_steps(dftu_handle h, void* psi, dftu_prec prec, int nbands, int64_t ld_band, const double* f,
+                              double dt, int order, int nsteps, dftu_stream stream) {
+    NvtxRange nvtx_range("dftu_taylor_steps");
+    Ctx* c = reinterpret_cast<Ctx*>(h);
+    if (!c) return DFTU_ERR_INVALID_ARG;
+    if (!c->atoms_ready) return fail(c, DFTU_ERR_NOT_READY, "taylor_steps: call dftu_setup_atoms first");
+    if (!psi || !f || (prec != DFTU_C128 && prec != DFTU_C64) || !valid_stride_args(c, nbands, ld_band) ||
+        order < 1 || order > MAX_TAYLOR || !std::isfinite(dt) || nsteps < 1)
+        return fail(c, DFTU_ERR_INVALID_ARG, "taylor_steps: null buffers, bad precision, band count, order, dt or step count");
+    for (size_t a = 0; a < c->atoms.size(); ++a)
+        if (std::isnan(c->h_fixU[a]) && !c->h_coul_set[c->atoms[a].species])
+            return fail(c, DFTU_ERR_NOT_READY, "taylor_steps: Coulomb integrals missing for an ACBN0 atom");
+    Guard g(c->device);
+    int64_t sk, ss, sn;
+    strides(c, nbands, ld_band, sk, ss, sn);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!gpu_addressable(c->device, psi, st)) return fail(c, DFTU_ERR_INVALID_ARG, "taylor_steps: the states are not addressable by this GPU (device memory of another GPU, or pageable host memory on a device without pageable access)");
+    if (!gpu_addressable(c->device, f, st)) return fail(c, DFTU_ERR_INVALID_ARG, "taylor_steps: f is not addressable by this GPU");
+    const int vp = c->variant[prec == DFTU_C64 ? 1 : 0], va = c->variant[prec == DFTU_C64 ? 3 : 2];
+    const bool G = c->gauge_on;
+    // complex64 collinear states without a vector potential: the scatter of each step also gathers the
+    // updated states on the final tiles, and a projection of the remaining tiles completes the gather
+    const bool fused = prec == DFTU_C64 && c->spin != DFTU_NONCOLLINEAR && !G;
+    View sub = c->v;
+    sub.tiles = c->d_nonfinal_tiles;
+    sub.ntiles = c->n_nonfinal;
+    cudaError_t e = launch_project(c->v, psi, prec, c->f64_mode, nbands, sk, ss, sn, vp, st, G);
+    if (e == cudaSuccess) e = launch_taylor_coefs(dt, order, c->d_taylor, st);
+    for (int step = 0; step < nsteps && e == cudaSuccess; ++step) {
+        e = launch_nbar(c->v, nbands, st);
+        if (e == cudaSuccess) e = launch_occupations(c->v, f, nbands, st);
+        if (e == cudaSuccess) e = launch_acbn0(c->v, st);
+        if (e == cudaSuccess) e = launch_taylor_cv(c->v, nbands, order, c->d_taylor, G, st);
+        if (e != cudaSuccess) break;
+        if (fused) {
+            e = launch_apply_project_c64(c->v, psi, nbands, sk, ss, sn, c->d_coef_one, c->d_color_order, c->color_beg, st);
+            if (e == cudaSuccess && sub.ntiles > 0) e = launch_project_c64_tiles(sub, psi, nbands, sk, ss, sn, st);
+            if (e == cudaSuccess) e = launch_tile_reduce(c->v, nbands, st);
+        } else {
+            e = launch_apply(c->v, psi, prec, c->f64_mode, nbands, sk, ss, sn, c->d_coef_one, c->d_color_order, c->color_beg, va, 1, st, G);
+            if (e == cudaSuccess) e = launch_project(c->v, psi, prec, c->f64_mode, nbands, sk, ss, sn, vp, st, G);
+        }
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "taylor_steps");
     c->last_stream = st;
     c->proj_ready = c->occ_ready = c->pot_ready = true;
     c->proj_nbands = nbands;

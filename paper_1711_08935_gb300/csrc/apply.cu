@@ -20,7 +20,10 @@ struct ApplyArgs {
     int accumulate;        // 1: psi += c V_U psi_proj ; 0: psi = c V_U psi_proj on the sphere points
 };
 
-enum APol { A_F64 = 0, A_PAIR = 1, A_F32 = 2, A_F32P = 3 };   // A_F32P: complex64, paired orbital rows
+// A_F32P: complex64, paired orbital rows.  A_F32PJ: the same apply, which also projects the updated values
+// of a final tile (Tile_final) onto its orbitals: the gather of the next real-time step fused into this
+// step's scatter (dftu_taylor_steps).
+enum APol { A_F64 = 0, A_PAIR = 1, A_F32 = 2, A_F32P = 3, A_F32PJ = 4 };
 
 // (hi, lo) float split of a double (round-to-nearest hi, exact-ish remainder) -- used only for the
 // per-CTA coefficients, so the FP64 conversion cost is negligible.
@@ -309,6 +312,101 @@ __device__ __forceinline__ void apply_body(const Tile& t, const ApplyArgs& a, in
     }
 }
 
+// A_F32PJ: the A_F32P read-modify-write with orbital rows [hi pairs | lo pairs] per point; with PROJ the
+// updated value x of every point is also projected, p_m += (phi_hi + phi_lo)_m x, both halves folded into
+// one FP32 sum per orbital by two fused multiply-adds (the compensated products of the complex64
+// projection).  The sums run over the lane's points, then over the Q lanes of the band; the tile's
+// partial sums are written in FP64 without the Bloch phase, in the layout k_tile_reduce reads.
+// Every lane of the warp calls it (the lane sums are combined with shuffles); lanes whose band is past
+// nbands (active = false) touch no memory.
+template <int Q, int M, int U, int PF, int PROJ>
+__device__ __forceinline__ void apply_project_body(const View& v, const Tile& t, const ApplyArgs& a, int64_t off, int q,
+                                                   int bl, int ks, int band, bool active, const int* s_idx,
+                                                   const unsigned char* s_first, const unsigned char* after_idx,
+                                                   const unsigned char* after_c) {
+    constexpr int MP = (M + 1) & ~1, NP = MP / 2;
+    float2* row = reinterpret_cast<float2*>(a.psi) + off;
+    const float* s_phf = reinterpret_cast<const float*>(after_c);
+    const float2* s_c = reinterpret_cast<const float2*>(after_idx);
+    float2 cre[NP], cim[NP], Sr[NP], Si[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        const float2 c0 = s_c[bl * MAXM + 2 * j];
+        const float2 c1 = (2 * j + 1 < M) ? s_c[bl * MAXM + 2 * j + 1] : make_float2(0.f, 0.f);
+        cre[j] = make_float2(c0.x, c1.x);
+        cim[j] = make_float2(c0.y, c1.y);
+        Sr[j] = make_float2(0.f, 0.f);
+        Si[j] = make_float2(0.f, 0.f);
+    }
+    const int np = active ? t.np : 0;
+    for (int i0 = q; i0 < np; i0 += Q * U) {
+        float2 x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            int i = i0 + u * Q;
+            x[u] = (i < np && (a.accumulate || !s_first[i])) ? row[s_idx[i]] : make_float2(0.f, 0.f);
+        }
+        if (PF) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                int i = i0 + Q * U + u * Q;
+                if (i < np) asm volatile("prefetch.global.L2 [%0];" ::"l"(row + s_idx[i]));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const float* ph = s_phf + (i0 + u * Q) * (2 * MP);
+            float2 ar = make_float2(0.f, 0.f), ai = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                const float2 f2 = *reinterpret_cast<const float2*>(ph + 2 * j);
+                ar = __ffma2_rn(f2, cre[j], ar);
+                ai = __ffma2_rn(f2, cim[j], ai);
+            }
+            x[u] = __fadd2_rn(x[u], make_float2(ar.x + ar.y, ai.x + ai.y));
+            if (PROJ) {   // rows past the tile are zeros, so the padded points add nothing
+                const float2 r = make_float2(x[u].x, x[u].x), m = make_float2(x[u].y, x[u].y);
+#pragma unroll
+                for (int j = 0; j < NP; ++j) {
+                    const float2 h2 = *reinterpret_cast<const float2*>(ph + 2 * j);
+                    const float2 l2 = *reinterpret_cast<const float2*>(ph + MP + 2 * j);
+                    Sr[j] = __ffma2_rn(l2, r, __ffma2_rn(h2, r, Sr[j]));
+                    Si[j] = __ffma2_rn(l2, m, __ffma2_rn(h2, m, Si[j]));
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            int i = i0 + u * Q;
+            if (i < np) row[s_idx[i]] = x[u];
+        }
+    }
+    if (PROJ) {
+#pragma unroll
+        for (int o = Q / 2; o > 0; o >>= 1)
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                Sr[j] = __fadd2_rn(Sr[j], make_float2(__shfl_xor_sync(0xffffffffu, Sr[j].x, o), __shfl_xor_sync(0xffffffffu, Sr[j].y, o)));
+                Si[j] = __fadd2_rn(Si[j], make_float2(__shfl_xor_sync(0xffffffffu, Si[j].x, o), __shfl_xor_sync(0xffffffffu, Si[j].y, o)));
+            }
+        // every lane of the band's group holds the sums; lane q writes orbital q (and q + Q, ...)
+#pragma unroll
+        for (int m0 = 0; m0 < M; m0 += Q) {
+            const int mq = m0 + q;
+            if (active && mq < M) {
+                float re = Sr[0].x, im = Si[0].x;
+#pragma unroll
+                for (int mm = 1; mm < M; ++mm)
+                    if (mm == mq) {
+                        re = (mm & 1) ? Sr[mm / 2].y : Sr[mm / 2].x;
+                        im = (mm & 1) ? Si[mm / 2].y : Si[mm / 2].x;
+                    }
+                v.part[((int64_t)ks * v.TM + t.moff + mq) * v.max_bands + band] = make_double2(f2d_bits(re), f2d_bits(im));
+            }
+        }
+    }
+}
+
 // One work item: tile `tile_id` (a tile of the current colour) of the system (v, a), component ks, band chunk `chunk`.
 template <int POL, int Q, int NBG, int U, int PF, int G>
 __device__ __forceinline__ void apply_item(const View& v, const ApplyArgs& a, int tile_id, int ks, int chunk,
@@ -340,6 +438,15 @@ __device__ __forceinline__ void apply_item(const View& v, const ApplyArgs& a, in
         for (int e = threadIdx.x; e < TILE_PAD * MP; e += CTA) {
             const int i = e / MP, m = e - i * MP;
             s_phf[e] = (i < t.np && m < M) ? v.phi_hi[t.phi0 + (int64_t)i * M + m] : 0.f;
+        }
+    } else if (POL == A_F32PJ) {
+        float* s_phf = reinterpret_cast<float*>(after_c);
+        const int MP = (M + 1) & ~1;
+        for (int e = threadIdx.x; e < TILE_PAD * MP; e += CTA) {
+            const int i = e / MP, m = e - i * MP;
+            const bool in = i < t.np && m < M;
+            s_phf[i * 2 * MP + m] = in ? v.phi_hi[t.phi0 + (int64_t)i * M + m] : 0.f;
+            s_phf[i * 2 * MP + MP + m] = in ? v.phi_lo[t.phi0 + (int64_t)i * M + m] : 0.f;
         }
     } else {
         float4* s_phi = reinterpret_cast<float4*>(after_c);
@@ -392,7 +499,28 @@ __device__ __forceinline__ void apply_item(const View& v, const ApplyArgs& a, in
         }
         __syncthreads();
         const int band = band0 + bl;
-        if (band < a.nbands) {
+        if constexpr (POL == A_F32PJ) {
+            const bool active = band < a.nbands;
+            const int64_t off = active ? (int64_t)k * a.sk + (int64_t)s * a.ss + (int64_t)band * a.sn : 0;
+            const int qq = lane & (Q - 1);
+#define DFTU_PJ(MM, PR) apply_project_body<Q, MM, U, PF, PR>(v, t, a, off, qq, bl, ks, band, active, s_idx, s_first, after_idx, after_c)
+            if (v.tile_final[tile_id]) {
+                switch (M) {
+                    case 1: DFTU_PJ(1, 1); break;
+                    case 3: DFTU_PJ(3, 1); break;
+                    case 5: DFTU_PJ(5, 1); break;
+                    default: DFTU_PJ(7, 1); break;
+                }
+            } else {
+                switch (M) {
+                    case 1: DFTU_PJ(1, 0); break;
+                    case 3: DFTU_PJ(3, 0); break;
+                    case 5: DFTU_PJ(5, 0); break;
+                    default: DFTU_PJ(7, 0); break;
+                }
+            }
+#undef DFTU_PJ
+        } else if (band < a.nbands) {
             const int64_t off = (int64_t)k * a.sk + (int64_t)s * a.ss + (int64_t)band * a.sn;
             const int pe = s_pe;
             switch (M) {
@@ -495,6 +623,15 @@ cudaError_t launch_apply(const View& v, void* psi, dftu_prec prec, dftu_f64_mode
     }
 #undef DFTU_CASE_F32
 #undef DFTU_CASE_PAIR
+}
+
+// The complex64 scatter of dftu_taylor_steps, fused with the next step's gather on the final tiles: the
+// default complex64 apply shape (16 lanes per band, 8 points in flight, L2 prefetch).
+cudaError_t launch_apply_project_c64(const View& v, void* psi, int nbands, int64_t sk, int64_t ss, int64_t sn,
+                                     const double* coef, const int* color_order, const std::vector<int>& color_beg,
+                                     cudaStream_t st) {
+    ApplyArgs a{psi, sk, ss, sn, nbands, coef, nullptr, 1};
+    return run_apply<A_F32PJ, 16, 4, 8, 1>(v, a, color_order, color_beg, st);
 }
 
 // cv[ks][band][moff_I + m] = sum_m' V^I_mm' p_m' (collinear: the spin block of ks; non-collinear: the

@@ -78,6 +78,7 @@ struct View {
     const int* species_M;
 
     const Tile* tiles;
+    const unsigned char* tile_final;   // [ntiles] 1 if no tile of a later apply colour covers any of its points
     // The projection's own tiling: the same image segments cut into tiles of up to PTILE points (half
     // the tile epilogues and partial sums of TILE-point tiles).  A projection launch that uses it swaps
     // these into its copy of the View for tiles, ntiles, TM and atom_tile_beg/end, so k_tile_reduce
@@ -167,6 +168,8 @@ struct Ctx {
     View v{};
     std::vector<void*> allocs;   // every device allocation, freed by dftu_destroy
     int* d_color_order = nullptr;
+    Tile* d_nonfinal_tiles = nullptr;   // copies of the tiles that are not final (tile_final == 0), colour order
+    int n_nonfinal = 0;
     double* d_coef_one = nullptr;
     double* d_taylor = nullptr;      // [MAX_TAYLOR] complex Taylor coefficients -i dt / j
     double* d_forces = nullptr;      // [natoms][3]
@@ -221,6 +224,17 @@ cudaError_t launch_apply(const View& v, void* psi, dftu_prec prec, dftu_f64_mode
                          int64_t sk, int64_t ss, int64_t sn, const double* coef, const int* color_order,
                          const std::vector<int>& color_beg, int variant, int accumulate, cudaStream_t st,
                          bool gauge = false);
+// The complex64 scatter (accumulate, coefficient coef) fused with the gather of the updated states on the
+// final tiles (View::tile_final): their partial sums land in v.part (TILE tiling) as a projection writes them.
+cudaError_t launch_apply_project_c64(const View& v, void* psi, int nbands, int64_t sk, int64_t ss, int64_t sn,
+                                     const double* coef, const int* color_order, const std::vector<int>& color_beg,
+                                     cudaStream_t st);
+// Complex64 projection partial sums of the tiles of `sub` only (a View whose tiles are a subset of the TILE
+// tiling, with that tiling's TM), without the tile reduce.
+cudaError_t launch_project_c64_tiles(const View& sub, const void* psi, int nbands, int64_t sk, int64_t ss, int64_t sn,
+                                     cudaStream_t st);
+// p from the partial sums of v's tiling (Bloch phase per segment, dV).
+cudaError_t launch_tile_reduce(const View& v, int nbands, cudaStream_t st);
 cudaError_t launch_gauge_phases(const View& v, const double* A, cudaStream_t st);
 // cv = V p for the first nbands bands (the coefficients the apply scatters).
 cudaError_t launch_coefvec(const View& v, int nbands, cudaStream_t st);

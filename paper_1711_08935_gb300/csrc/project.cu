@@ -883,6 +883,18 @@ cudaError_t launch_project(const View& v, const void* psi, dftu_prec prec, dftu_
     return cudaGetLastError();
 }
 
+cudaError_t launch_project_c64_tiles(const View& sub, const void* psi, int nbands, int64_t sk, int64_t ss, int64_t sn,
+                                     cudaStream_t st) {
+    ProjArgs a{psi, sk, ss, sn, nbands};
+    return run_project<P_F32B2F, 16, 8, 4, 0, 3, 0, 1, 256, TILE>(sub, a, st);
+}
+
+cudaError_t launch_tile_reduce(const View& v, int nbands, cudaStream_t st) {
+    int64_t n = (int64_t)v.nk * v.ns * nbands * v.MT;
+    k_tile_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(v, nbands);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_project_dirs(const View& v, const void* psi, dftu_prec prec, dftu_f64_mode mode, int nbands,
                                 int64_t sk, int64_t ss, int64_t sn, bool gauge, double2* p_out, int64_t p_stride,
                                 cudaStream_t st) {

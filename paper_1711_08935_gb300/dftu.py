@@ -31,7 +31,7 @@ EXPORTED = ["dftu_create", "dftu_setup_atoms", "dftu_get_sphere", "dftu_coulomb_
             "dftu_get_results", "dftu_get_renormalized", "dftu_get_projections", "dftu_total_orbitals",
             "dftu_atom_points", "dftu_sync_status", "dftu_last_error", "dftu_destroy",
             "dftu_set_kernel_variant", "dftu_kernel_variants", "dftu_project_sphere_noalloc",
-            "dftu_taylor_step", "dftu_batch_create", "dftu_batch_bind", "dftu_batch_project",
+            "dftu_taylor_step", "dftu_taylor_steps", "dftu_batch_create", "dftu_batch_bind", "dftu_batch_project",
             "dftu_batch_occupations", "dftu_batch_acbn0_uj", "dftu_batch_apply", "dftu_batch_last_error",
             "dftu_batch_destroy", "dftu_forces", "dftu_radius_cell", "dftu_radius_threshold",
             "dftu_set_vector_potential", "dftu_hubbard_current", "dftu_fll_energy", "dftu_occupation_elems",
@@ -81,6 +81,7 @@ def load() -> C.CDLL:
         "dftu_acbn0_uj": [vp, vp],
         "dftu_apply": [vp, vp, i32, i32, i64, vp, i32, vp],
         "dftu_taylor_step": [vp, vp, vp, i32, i32, i64, vp, d, i32, vp],
+        "dftu_taylor_steps": [vp, vp, i32, i32, i64, vp, d, i32, i32, vp],
         "dftu_batch_create": [C.POINTER(vp), i32, C.POINTER(vp)],
         "dftu_batch_bind": [vp, C.POINTER(vp), i32, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(vp)],
         "dftu_batch_project": [vp, vp],
@@ -346,6 +347,13 @@ class Handle:
         wp = C.c_void_p(work.data_ptr()) if work is not None else None
         self._check(self.lib.dftu_taylor_step(self.h, C.c_void_p(psi.data_ptr()), wp, prec, nb, ld,
                                               self._f_arg(f), float(dt), int(order), _stream_ptr(stream, self.device)))
+
+    def taylor_steps(self, psi: torch.Tensor, f: torch.Tensor, dt: float, nsteps: int, order: int = 4, stream=None):
+        """nsteps real-time steps (dftu_taylor_steps): for complex64 collinear states the scatter of each
+        step also gathers the updated states for the next one."""
+        prec, nb, ld = self._psi_args(psi)
+        self._check(self.lib.dftu_taylor_steps(self.h, C.c_void_p(psi.data_ptr()), prec, nb, ld, self._f_arg(f),
+                                               float(dt), int(order), int(nsteps), _stream_ptr(stream, self.device)))
 
     # ------------------------------------------------------------------ results
     def _mat_sizes(self):
