@@ -632,10 +632,12 @@ def run_rt(args):
     # kernel shapes tuned on these states (the tuner's applies go into a scratch buffer freed afterwards)
     from paper_1711_08935_gb300.autotune import autotune
     h.project(psi); h.occupations(f); h.acbn0_uj()
-    scratch = torch.zeros_like(psi)
-    tuned = autotune(h, psi, out=scratch)
-    del scratch
-    torch.cuda.empty_cache()
+    tuned = None
+    if not args.no_tune:
+        scratch = torch.zeros_like(psi)
+        tuned = autotune(h, psi, out=scratch)
+        del scratch
+        torch.cuda.empty_cache()
     n0 = (psi.abs() ** 2).sum(-1).double() * s.grid.dV
     dt = 0.01
     S = _sphere_bytes(h, len(s.atoms))

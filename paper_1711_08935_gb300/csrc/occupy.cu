@@ -11,33 +11,31 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ double2 cmulc(double2 a, double2 b) { return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y); }  // a conj(b)
 
 // Eq. (9): Nbar per state = sum over atoms of the state's species-mates and m (and spinor components) of |p|^2.
-// One thread per (state, species).
-__device__ __forceinline__ void nbar_elem(const View& v, int nbands, int64_t g) {
-    int rows = v.noncollinear ? v.nk : v.nk * v.ns;
-    if (g >= (int64_t)rows * nbands * v.nspecies) return;
-    const int sp = (int)(g % v.nspecies);
-    g /= v.nspecies;
-    int row = (int)(g / nbands), band = (int)(g % nbands);
-    {
-        double acc = 0.0;
-        for (int a = 0; a < v.natoms; ++a) {
-            if (v.atom_species[a] != sp) continue;
-            int M = v.atom_M[a], mo = v.atom_moff[a];
-            int ncomp = v.noncollinear ? 2 : 1;
-            for (int c = 0; c < ncomp; ++c) {
-                int ks = v.noncollinear ? row * 2 + c : row;
-                const double2* pr = v.p + ((int64_t)ks * v.max_bands + band) * v.MT + mo;
-                for (int m = 0; m < M; ++m) acc += pr[m].x * pr[m].x + pr[m].y * pr[m].y;
-            }
-        }
-        v.nbar[((int64_t)row * v.max_bands + band) * v.nspecies + sp] = acc;
+// One warp per (state, species): the lanes stride over the state's row of projections (coalesced), keep
+// the orbitals of that species, and the lane sums are added by a fixed butterfly.
+__device__ __forceinline__ void nbar_warp(const View& v, int nbands, int64_t w) {
+    const int rows = v.noncollinear ? v.nk : v.nk * v.ns;
+    if (w >= (int64_t)rows * nbands * v.nspecies) return;   // uniform over the warp
+    const int lane = threadIdx.x & 31;
+    const int sp = (int)(w % v.nspecies);
+    w /= v.nspecies;
+    const int row = (int)(w / nbands), band = (int)(w % nbands);
+    const int ncomp = v.noncollinear ? 2 : 1;
+    double acc = 0.0;
+    for (int c = 0; c < ncomp; ++c) {
+        const int ks = v.noncollinear ? row * 2 + c : row;
+        const double2* pr = v.p + ((int64_t)ks * v.max_bands + band) * v.MT;
+        for (int j = lane; j < v.MT; j += 32)
+            if (v.atom_species[v.orb_atom[j]] == sp) acc += pr[j].x * pr[j].x + pr[j].y * pr[j].y;
     }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) v.nbar[((int64_t)row * v.max_bands + band) * v.nspecies + sp] = acc;
 }
 
-__global__ void k_nbar(View v, int nbands) { nbar_elem(v, nbands, (int64_t)blockIdx.x * blockDim.x + threadIdx.x); }
+__global__ void k_nbar(View v, int nbands) { nbar_warp(v, nbands, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); }
 
 __global__ void k_nbar_batch(const View* __restrict__ views, const ProjArgs* __restrict__ args) {
-    nbar_elem(views[blockIdx.y], args[blockIdx.y].nbands, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    nbar_warp(views[blockIdx.y], args[blockIdx.y].nbands, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
 }
 
 // Eqs. (4), (8), (A2), (B3).  The (k, band) sum of every (atom, spin channel) [collinear] or atom
@@ -402,8 +400,8 @@ cudaError_t launch_fll(const View& v, double* out, cudaStream_t st) {
 
 cudaError_t launch_nbar(const View& v, int nbands, cudaStream_t st) {
     int rows = v.noncollinear ? v.nk : v.nk * v.ns;
-    int64_t n = (int64_t)rows * nbands * v.nspecies;
-    k_nbar<<<(unsigned)((n + 63) / 64), 64, 0, st>>>(v, nbands);
+    int64_t n = (int64_t)rows * nbands * v.nspecies;   // warps, 8 per CTA
+    k_nbar<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(v, nbands);
     return cudaGetLastError();
 }
 
@@ -422,8 +420,8 @@ cudaError_t launch_acbn0(const View& v, cudaStream_t st) {
 }
 
 cudaError_t launch_occupations_batch(const BatchLaunch& b, cudaStream_t st) {
-    dim3 g1((unsigned)((b.max_rows_nbar + 63) / 64), b.nsys);
-    k_nbar_batch<<<g1, 64, 0, st>>>(b.views, b.args);
+    dim3 g1((unsigned)((b.max_rows_nbar + 7) / 8), b.nsys);   // one warp per (state, species), 8 per CTA
+    k_nbar_batch<<<g1, 256, 0, st>>>(b.views, b.args);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     dim3 g2(b.max_atoms, b.max_ns * OCC_SPLIT, b.nsys);

@@ -67,10 +67,10 @@ __global__ void __launch_bounds__(128) k_taylor_cv(View v, int nbands, int order
             if (!v.noncollinear) {
                 const double2* Vm = v.V + vo + (int64_t)s0 * M * M + m * M;
                 const double2* pr = xin + vrow(0) + mo;
-                for (int qq = 0; qq < M; ++qq) {
+                for (int qq = 0; qq < M; ++qq) {   // four fused multiply-adds per complex product
                     const double2 A = Vm[qq], B = pr[qq];
-                    re += A.x * B.x - A.y * B.y;
-                    im += A.x * B.y + A.y * B.x;
+                    re = fma(A.x, B.x, fma(-A.y, B.y, re));
+                    im = fma(A.x, B.y, fma(A.y, B.x, im));
                 }
             } else {
                 const double2* Vm = v.V + vo + (int64_t)(c * M + m) * (2 * M);
@@ -78,8 +78,8 @@ __global__ void __launch_bounds__(128) k_taylor_cv(View v, int nbands, int order
                     const double2* pr = xin + vrow(c2) + mo;
                     for (int qq = 0; qq < M; ++qq) {
                         const double2 A = Vm[c2 * M + qq], B = pr[qq];
-                        re += A.x * B.x - A.y * B.y;
-                        im += A.x * B.y + A.y * B.x;
+                        re = fma(A.x, B.x, fma(-A.y, B.y, re));
+                        im = fma(A.x, B.y, fma(A.y, B.x, im));
                     }
                 }
             }
@@ -109,8 +109,8 @@ __global__ void __launch_bounds__(128) k_taylor_cv(View v, int nbands, int order
                         ti = fma(B[q], x.y, ti);
                     }
                     const double2 ph = v.blk_phase[k * v.nblk + b];
-                    re += ph.x * tr - ph.y * ti;
-                    im += ph.x * ti + ph.y * tr;
+                    re = fma(ph.x, tr, fma(-ph.y, ti, re));
+                    im = fma(ph.x, ti, fma(ph.y, tr, im));
                 }
                 X[vrow(c) + j] = cmul(cj, make_double2(re, im));
             }
