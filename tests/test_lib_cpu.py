@@ -34,6 +34,8 @@ def test_null_handle_calls_are_rejected(lib):
     assert lib.dftu_occupations(None, None, None) == 1
     assert lib.dftu_acbn0_uj(None, None) == 1
     assert lib.dftu_apply(None, None, 0, 1, 1, None, 1, None) == 1
+    assert lib.dftu_taylor_step(None, None, None, 0, 1, 1, None, 0.01, 4, None) == 1
+    assert lib.dftu_taylor_steps(None, None, 0, 1, 1, None, 0.01, 4, 10, None) == 1
     assert lib.dftu_sync_status(None) == 1
     assert lib.dftu_last_error(None) == b"null handle"
     lib.dftu_destroy(None)
